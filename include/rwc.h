@@ -1,0 +1,267 @@
+/*
+ * rwc.h -- C ABI of the GB300 FastWalk library (random walk centrality by
+ * sampling rooted spanning trees).
+ *
+ * Paper: "Efficient Algorithms for Computing Random Walk Centrality"
+ * (arXiv 2510.20604).  The library implements the data-parallel path of
+ * FastWalk (Section 5, Algorithm 3) together with the pivot solve and
+ * recovery of Algorithm 1 (AppRWC, Section 3), a gradient of the exact
+ * centrality with respect to the edge weights, and a batched sampler for
+ * many small graphs.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns an rwc_status; RWC_OK (0) on success.  On any
+ *    other value rwc_last_error() returns a message for the calling thread.
+ *  - Buffers named host_* are host memory; every other pointer argument is
+ *    device memory (for instance a torch tensor's data_ptr()).  The caller
+ *    owns all of them.  The library copies graphs into device memory that it
+ *    owns and frees in the matching *_destroy call.
+ *  - stream is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    enqueued on it; entry points that must inspect device results
+ *    (rwc_sample_trees, rwc_estimate, rwc_grad, rwc_batch_sample) synchronise
+ *    that stream before returning, so their outputs are ready on return.
+ *  - Graphs are undirected, given as CSR with both arc directions: row u
+ *    lists the neighbours of u.  Vertex ids are int32; n >= 2.
+ *  - All functions are safe to call from several host threads on distinct
+ *    handles; a single handle must not be used concurrently.
+ */
+#ifndef RWC_H
+#define RWC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t rwc_status;
+enum {
+    RWC_OK = 0,
+    RWC_ERR_INVALID = 1,        /* malformed argument or graph */
+    RWC_ERR_NOT_CONNECTED = 2,  /* graph has more than one component */
+    RWC_ERR_OOM = 3,            /* device or host allocation failed */
+    RWC_ERR_NOT_CONVERGED = 4,  /* an iteration cap was reached */
+    RWC_ERR_CUDA = 5,           /* a CUDA call failed */
+    RWC_ERR_UNSUPPORTED = 6     /* valid request this build cannot serve */
+};
+
+typedef struct CUstream_st *rwc_stream_t;   /* same type as cudaStream_t */
+typedef struct rwc_graph rwc_graph_t;
+typedef struct rwc_batch rwc_batch_t;
+
+/* Flags for rwc_graph_create. */
+#define RWC_GRAPH_INT64_OFFSETS 0x1u  /* keep arc offsets as int64 on the device
+                                         (always used when nnz >= 2^31) */
+#define RWC_GRAPH_SKIP_CONNECTIVITY 0x2u  /* caller guarantees connectivity */
+
+typedef struct {
+    int64_t n;          /* vertices */
+    int64_t nnz;        /* arcs (2 x undirected edges) */
+    int32_t root;       /* pivot v used as the root of every tree */
+    int32_t weighted;   /* 1 if weights were given (alias tables built) */
+    int32_t offsets64;  /* 1 if arc offsets are int64 on the device */
+    int32_t reserved;
+    double vol;         /* sum of weighted degrees (the paper's 2m) */
+    double dmax;        /* largest weighted degree */
+    int64_t device_bytes;  /* device memory held by the graph */
+} rwc_graph_info_t;
+
+/* Sampler modes for rwc_options_t.mode. */
+#define RWC_MODE_AUTO 0
+#define RWC_MODE_GLOBAL 1   /* rounds over tree chunks, state in HBM */
+#define RWC_MODE_SHARED 2   /* one thread block per tree, state in shared memory */
+
+typedef struct {
+    int32_t mode;             /* RWC_MODE_*; AUTO picks SHARED when the tree fits */
+    int32_t max_rounds;       /* cap on popping rounds per chunk (0 = 1<<22) */
+    int64_t trees_per_chunk;  /* GLOBAL mode: trees resident at once (0 = auto) */
+    int32_t use_jumps;        /* GLOBAL mode: 1 = jump pointers (default), 0 = off,
+                                 -1 = default */
+    int32_t block_threads;    /* SHARED mode block size (0 = auto) */
+    int64_t memory_budget;    /* GLOBAL mode: bytes of scratch to use (0 = auto) */
+    int32_t profile;          /* 1 = time every kernel launch with CUDA events on
+                                 the call's stream (fills rwc_stats_t.phase_*) */
+    int32_t reserved;
+} rwc_options_t;
+
+/* Sampler phases reported in rwc_stats_t (GLOBAL mode; SHARED mode reports
+ * its single kernel as RWC_PHASE_WALK). */
+#define RWC_PHASE_INIT 0      /* first successor of every vertex */
+#define RWC_PHASE_WALK 1      /* marked vertex -> next marked or settled vertex */
+#define RWC_PHASE_CLASSIFY 2  /* cycle leaders on the compressed graph */
+#define RWC_PHASE_POP 3       /* pop cycles: new successor draws */
+#define RWC_PHASE_FINISH 4    /* return unpopped marks to the free pool */
+#define RWC_PHASE_ACCUM 5     /* visits into FP64 sums, optional tree output */
+#define RWC_NPHASE 6
+
+typedef struct {
+    int64_t trees;        /* trees sampled by the last call */
+    int64_t draws;        /* successor draws (= sum of visits over all trees) */
+    int64_t rounds;       /* popping rounds, summed over chunks */
+    int64_t walk_steps;   /* pointer-chasing steps of the cycle detection */
+    int64_t chunks;       /* tree chunks processed */
+    int32_t mode;         /* mode actually used */
+    int32_t reserved;
+    int64_t marked;       /* compressed-graph nodes over all rounds (= draws) */
+    /* with rwc_options_t.profile: device time (ms), launches and work units
+     * per phase; units are vertices (INIT, ACCUM), walk steps (WALK), marked
+     * entries (CLASSIFY, FINISH) and successor draws (POP). */
+    double phase_ms[RWC_NPHASE];
+    int64_t phase_launches[RWC_NPHASE];
+    int64_t phase_units[RWC_NPHASE];
+} rwc_stats_t;
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char *rwc_last_error(void);
+
+/* Library version string. */
+const char *rwc_version(void);
+
+/* Number of CUDA kernel launches this library has issued in this process
+ * (diagnostics; monotone, all threads). */
+int64_t rwc_launch_count(void);
+
+/*
+ * Graph store (Section 2.2: G = (V, E), degrees, L = D - A; weighted reading:
+ * d_u = sum of the weights of u's arcs, vol = sum_u d_u plays the role of 2m,
+ * the walk moves from u to w with probability w_uw / d_u).
+ *
+ * host_row_ptr: int64 [n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz.
+ * host_col_idx: int32 [nnz], neighbours of each row sorted ascending.
+ * host_w:       float [nnz] positive finite weights, or NULL for unit weights.
+ *               Arc (u,w) and arc (w,u) must carry equal weights.
+ * root:         pivot v; -1 selects the vertex of largest weighted degree
+ *               with ties to the smallest id (Section 6: "the node with the
+ *               highest degree is selected as the pivot").
+ * Validation: n >= 2, sorted rows, every arc has its reverse with equal
+ * weight (repeated arcs are allowed and act as one edge of summed weight),
+ * no self-loops, finite positive weights, connected (one BFS) unless
+ * RWC_GRAPH_SKIP_CONNECTIVITY.  Returns RWC_ERR_INVALID or
+ * RWC_ERR_NOT_CONNECTED without allocating on failure.
+ * Weighted graphs get one Vose alias table per row, built on the host in
+ * FP64 and stored on the device next to the arcs (16 B per arc).
+ */
+rwc_status rwc_graph_create(int64_t n, int64_t nnz, const int64_t *host_row_ptr,
+                            const int32_t *host_col_idx, const float *host_w,
+                            int32_t root, uint32_t flags, rwc_graph_t **out);
+rwc_status rwc_graph_info(const rwc_graph_t *g, rwc_graph_info_t *host_out);
+rwc_status rwc_graph_destroy(rwc_graph_t *g);
+
+/*
+ * Sample rooted spanning trees (Section 5, Algorithm 3, the loop over
+ * i = 1..l) and accumulate each vertex's visit count.
+ *
+ * Tree i (i = tree0 .. tree0 + num_trees - 1) is the tree that Wilson's
+ * algorithm rooted at the pivot produces when the c-th call of
+ * RandomNeighbor(u) in that tree returns succ(u, c, i): Philox-4x32-10 with
+ * counter (c, u, i, 0) and key (seed & 0xffffffff, seed >> 32), arc index
+ * j = floor(o0 * deg(u) / 2^32), and for weighted graphs arc j kept when
+ * o1 < thr_j, else its alias.  The result does not depend on the order in
+ * which start nodes are processed (Wilson's cycle-popping theorem), so the
+ * parallel sampler reproduces the sequential algorithm exactly.
+ *
+ * sums:    FP64 [n]; sums[u] += sum over the trees of visits_u (exact
+ *          integers), where visits_u is Algorithm 3's count for u (the number
+ *          of RandomNeighbor(u) calls); sums[root] is unchanged.
+ * parents: NULL or int32 [num_trees][n]; parent of u in tree tree0+t,
+ *          -1 for the root.
+ * visits:  NULL or int32 [num_trees][n]; per-tree visit counts (0 at root).
+ * opt:     NULL for defaults.  stats: NULL or host struct filled on return.
+ * Requires tree0 + num_trees <= 2^32.  Returns RWC_ERR_NOT_CONVERGED if
+ * max_rounds is reached (outputs then undefined).  Synchronises stream.
+ */
+rwc_status rwc_sample_trees(rwc_graph_t *g, uint64_t seed, int64_t tree0,
+                            int64_t num_trees, double *sums, int32_t *parents,
+                            int32_t *visits, const rwc_options_t *opt,
+                            rwc_stats_t *stats, rwc_stream_t stream);
+
+/*
+ * Algorithm 1 (AppRWC) fed by the estimator of Section 5.
+ *   t_u = sums[u] / num_trees                        (estimate of (NL_v^-1)_uu)
+ *   b   = sqrt(d_v) e_v - (sqrt(d_v) / vol) d        (line 1)
+ *   z   = L^+ b by Jacobi-preconditioned CG to relative residual cg_tol
+ *         (line 2, the paper's LapSolve; FP32 SpMV inner solves, FP64
+ *         residual refinement, z kept in FP64)
+ *   y_u = sqrt(d_u) z_u - sqrt(d_u) (sum_w d_w z_w) / vol   (line 3)
+ *   H_u = (t_u - (d_u/d_v) y_v + 2 sqrt(d_u/d_v) y_u) / pi_u, u != v (Eq. 3)
+ *   H_v = y_v / pi_v
+ * sums: FP64 [n] device; H_out: FP64 [n] device; y_out: NULL or FP64 [n].
+ * cg_tol <= 0 selects 1e-10.  Returns RWC_ERR_NOT_CONVERGED if the solver
+ * stalls.  Synchronises stream.
+ */
+rwc_status rwc_estimate(rwc_graph_t *g, const double *sums, int64_t num_trees,
+                        double cg_tol, double *H_out, double *y_out,
+                        rwc_stream_t stream);
+
+/*
+ * Recovery step only (Algorithm 1 lines 4-7) for a given pivot column y
+ * (FP64 [n] device): H from sums/num_trees and y as in rwc_estimate.
+ */
+rwc_status rwc_recover(rwc_graph_t *g, const double *sums, int64_t num_trees,
+                       const double *y, double *H_out, rwc_stream_t stream);
+
+/*
+ * Laplacian solve used by rwc_estimate and rwc_grad: X = L^+ B for k
+ * right-hand sides (block CG, Jacobi preconditioner, FP32 SpMM, FP64 dots
+ * and FP64 residual refinement; each column's mean is removed first).
+ * B, X: FP64 [k][n] device (column-major by right-hand side), may not alias.
+ * iters_out: NULL or host int, outer+inner iterations used.
+ */
+rwc_status rwc_solve(rwc_graph_t *g, int32_t k, const double *B, double *X,
+                     double tol, int32_t *iters_out, rwc_stream_t stream);
+
+/*
+ * Gradient of J(w) = sum_v c_v H_v(w) with respect to each undirected edge
+ * weight, H the exact random walk centrality (Section 2.3,
+ * H_v = vol L^+_vv - 2 (L^+ d)_v + d^T L^+ d / vol).  For edge e = (a, b),
+ * with x = L^+ c, y = L^+ d, Z = Q C^1/2 L^+:
+ *   dJ/dw_e = 2 tr(C L^+) - vol sum_i (Z_ia - Z_ib)^2
+ *             + 2 (x_a - x_b)(y_a - y_b) - 2 (x_a + x_b)
+ *             + (sum c) [ (2 (y_a + y_b) - (y_a - y_b)^2) / vol - 2 d^T y / vol^2 ]
+ * and tr(C L^+) estimated by tr(Z C^1/2 Q^T).  Q (k x n) is the
+ * Johnson-Lindenstrauss sketch: Q_iu = +-1/sqrt(k), the sign the top bit of
+ * Philox output o0 for counter (i, u, 0xFFFFFFFF, 0) and key sketch_seed;
+ * k = 0 means Q = I (exact, k = n right-hand sides; small graphs only).
+ * c: FP64 [n] device, c_u >= 0.  grad_w: FP32 [nnz/2] device, one entry per
+ * undirected edge in the order of arcs (a, b) with a < b in CSR order (the
+ * repeated arcs of a multi-edge each get the same value).
+ * Synchronises stream.
+ */
+rwc_status rwc_grad(rwc_graph_t *g, const double *c, int32_t k,
+                    uint64_t sketch_seed, double cg_tol, float *grad_w,
+                    rwc_stream_t stream);
+
+/*
+ * Batched sampler: many independent small graphs, all trees of all graphs in
+ * one persistent launch (captured in a CUDA graph when use_graph != 0).
+ * host_graph_offsets: int64 [G+1] vertex offsets of each graph inside the
+ * concatenated CSR; host_row_ptr: int64 [N+1] with global arc offsets;
+ * host_col_idx: int32 [nnz] LOCAL vertex ids (0..n_g-1); host_w NULL (unit
+ * weights) or float [nnz].  Every graph is validated as in rwc_graph_create
+ * and rooted at its own max-degree vertex.  Graph g's trees use Philox
+ * counter word 3 = g, so graph g of a batch reproduces rwc_sample_trees on
+ * that graph alone only for g = 0; the oracle reproduces every graph.
+ */
+rwc_status rwc_batch_create(int32_t G, const int64_t *host_graph_offsets,
+                            const int64_t *host_row_ptr,
+                            const int32_t *host_col_idx, const float *host_w,
+                            rwc_batch_t **out);
+/* sums: FP64 [N] device (per-vertex, graph g's block at its vertex offset),
+ * accumulated.  per_graph_launch != 0 issues one launch per graph instead of
+ * the persistent kernel (the baseline it is compared with).  roots_out: NULL
+ * or host int32 [G]. */
+rwc_status rwc_batch_sample(rwc_batch_t *b, uint64_t seed, int64_t trees_per_graph,
+                            double *sums, int32_t use_graph, int32_t per_graph_launch,
+                            rwc_stats_t *stats, rwc_stream_t stream);
+rwc_status rwc_batch_roots(const rwc_batch_t *b, int32_t *host_roots);
+/* Choose block size / trees per item for this batch by timing candidates on
+ * the device; results are cached in cache_path (JSON, may be NULL). */
+rwc_status rwc_autotune(rwc_batch_t *b, const char *cache_path, rwc_stream_t stream);
+rwc_status rwc_batch_destroy(rwc_batch_t *b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RWC_H */

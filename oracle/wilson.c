@@ -336,3 +336,18 @@ void oracle_wdeg(int64_t n, const int64_t *rp, const float *w, double *d)
         d[u] = s;
     }
 }
+
+/* Johnson-Lindenstrauss sketch Q (k x n, row-major) with Q_iu = +-1/sqrt(k):
+ * the sign is the top bit of Philox output o0 for counter (i, u, 0xFFFFFFFF, 0)
+ * and key (seed lo, seed hi) (set bit = negative). */
+void oracle_rademacher(int32_t k, int64_t n, uint64_t seed, double *Q)
+{
+    const uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    const double s = 1.0 / sqrt((double)k);
+    for (int32_t i = 0; i < k; ++i)
+        for (int64_t u = 0; u < n; ++u) {
+            uint32_t ctr[4] = { (uint32_t)i, (uint32_t)u, 0xFFFFFFFFu, 0u }, o[4];
+            oracle_philox4x32_10(ctr, key, o);
+            Q[(int64_t)i * n + u] = (o[0] >> 31) ? -s : s;
+        }
+}

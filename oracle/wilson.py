@@ -48,6 +48,8 @@ def lib():
         L.oracle_wilson_order.restype = _i64
         L.oracle_wdeg.argtypes = [_i64, _vp, _vp, _vp]
         L.oracle_wdeg.restype = None
+        L.oracle_rademacher.argtypes = [_i32, _i64, _u64, _vp]
+        L.oracle_rademacher.restype = None
         _lib = L
     return _lib
 
@@ -75,6 +77,13 @@ def alias_tables(g):
     if lib().oracle_alias_build(g.n, _p(rp), _p(w), _p(thr), _p(al)) != 0:
         raise MemoryError("oracle alias build")
     return thr, al
+
+
+def rademacher(k: int, n: int, seed: int) -> np.ndarray:
+    """k x n sketch of +-1/sqrt(k) signs drawn from Philox (see wilson.c)."""
+    Q = np.zeros((k, n), np.float64)
+    lib().oracle_rademacher(int(k), int(n), int(seed), _p(Q))
+    return Q
 
 
 def wdeg(g) -> np.ndarray:

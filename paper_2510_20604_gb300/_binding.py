@@ -1,0 +1,251 @@
+"""ctypes marshalling for ``include/rwc.h``.  No computation happens here."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+lib_path = os.path.join(HERE, "librwc.so")
+
+MODE_AUTO, MODE_GLOBAL, MODE_SHARED = 0, 1, 2
+NPHASE = 6
+PHASES = ("init", "walk", "classify", "pop", "finish", "accum")
+GRAPH_INT64_OFFSETS, GRAPH_SKIP_CONNECTIVITY = 0x1, 0x2
+_STATUS = {0: "OK", 1: "INVALID", 2: "NOT_CONNECTED", 3: "OOM", 4: "NOT_CONVERGED",
+           5: "CUDA", 6: "UNSUPPORTED"}
+
+
+class RWCError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"rwc status {status} ({_STATUS.get(status, '?')}): {msg}")
+        self.status = status
+
+
+class GraphInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("root", ctypes.c_int32),
+                ("weighted", ctypes.c_int32), ("offsets64", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("vol", ctypes.c_double), ("dmax", ctypes.c_double),
+                ("device_bytes", ctypes.c_int64)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
+                ("trees_per_chunk", ctypes.c_int64), ("use_jumps", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32), ("memory_budget", ctypes.c_int64),
+                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def __init__(self, mode=0, max_rounds=0, trees_per_chunk=0, use_jumps=-1, block_threads=0,
+                 memory_budget=0, profile=0):
+        super().__init__(mode, max_rounds, trees_per_chunk, use_jumps, block_threads,
+                         memory_budget, profile, 0)
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("trees", ctypes.c_int64), ("draws", ctypes.c_int64), ("rounds", ctypes.c_int64),
+                ("walk_steps", ctypes.c_int64), ("chunks", ctypes.c_int64), ("mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("marked", ctypes.c_int64),
+                ("phase_ms", ctypes.c_double * NPHASE), ("phase_launches", ctypes.c_int64 * NPHASE),
+                ("phase_units", ctypes.c_int64 * NPHASE)]
+
+    def as_dict(self):
+        out = {}
+        for f, _ in self._fields_:
+            if f == "reserved":
+                continue
+            v = getattr(self, f)
+            out[f] = list(v) if f.startswith("phase_") else v
+        return out
+
+
+_lib = None
+_vp, _i64, _i32, _u32, _u64, _d = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                   ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double)
+
+
+def lib():
+    """Load librwc.so (raises RWCError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(lib_path):
+        raise RWCError(5, f"CUDA library not built: {lib_path} is missing "
+                          "(run __graft_entry__.build())")
+    L = ctypes.CDLL(lib_path)
+    sig = {
+        "rwc_last_error": ([], ctypes.c_char_p),
+        "rwc_version": ([], ctypes.c_char_p),
+        "rwc_launch_count": ([], ctypes.c_int64),
+        "rwc_graph_create": ([_i64, _i64, _vp, _vp, _vp, _i32, _u32, ctypes.POINTER(_vp)], _i32),
+        "rwc_graph_info": ([_vp, ctypes.POINTER(GraphInfo)], _i32),
+        "rwc_graph_destroy": ([_vp], _i32),
+        "rwc_sample_trees": ([_vp, _u64, _i64, _i64, _vp, _vp, _vp, ctypes.POINTER(Options),
+                              ctypes.POINTER(Stats), _vp], _i32),
+        "rwc_estimate": ([_vp, _vp, _i64, _d, _vp, _vp, _vp], _i32),
+        "rwc_recover": ([_vp, _vp, _i64, _vp, _vp, _vp], _i32),
+        "rwc_solve": ([_vp, _i32, _vp, _vp, _d, ctypes.POINTER(_i32), _vp], _i32),
+        "rwc_grad": ([_vp, _vp, _i32, _u64, _d, _vp, _vp], _i32),
+        "rwc_batch_create": ([_i32, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)], _i32),
+        "rwc_batch_sample": ([_vp, _u64, _i64, _vp, _i32, _i32, ctypes.POINTER(Stats), _vp], _i32),
+        "rwc_batch_roots": ([_vp, _vp], _i32),
+        "rwc_autotune": ([_vp, ctypes.c_char_p, _vp], _i32),
+        "rwc_batch_destroy": ([_vp], _i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _check(st: int):
+    if st != 0:
+        raise RWCError(st, lib().rwc_last_error().decode())
+
+
+def _dptr(x, dtype=None, name="buffer"):
+    """Device pointer of a torch CUDA tensor (or an int), None for None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    import torch
+    if not isinstance(x, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch CUDA tensor")
+    if not x.is_cuda:
+        raise ValueError(f"{name}: must be a CUDA tensor")
+    if not x.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if dtype is not None and x.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {x.dtype}")
+    return x.data_ptr()
+
+
+def _hptr(a, dtype):
+    if a is None:
+        return None, None
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:  # pragma: no cover
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def rwc_version() -> str:
+    return lib().rwc_version().decode()
+
+
+def rwc_launch_count() -> int:
+    return int(lib().rwc_launch_count())
+
+
+def rwc_last_error() -> str:
+    return lib().rwc_last_error().decode()
+
+
+def rwc_graph_create(n, nnz, row_ptr, col_idx, w=None, root=-1, flags=0):
+    rp, prp = _hptr(row_ptr, np.int64)
+    ci, pci = _hptr(col_idx, np.int32)
+    ww, pw = _hptr(w, np.float32)
+    out = _vp()
+    _check(lib().rwc_graph_create(int(n), int(nnz), prp, pci, pw, int(root), int(flags),
+                                  ctypes.byref(out)))
+    return out.value
+
+
+def rwc_graph_info(g) -> GraphInfo:
+    info = GraphInfo()
+    _check(lib().rwc_graph_info(g, ctypes.byref(info)))
+    return info
+
+
+def rwc_graph_destroy(g):
+    _check(lib().rwc_graph_destroy(g))
+
+
+def rwc_sample_trees(g, seed, tree0, num_trees, sums, parents=None, visits=None, opt=None,
+                     stream=None) -> Stats:
+    import torch
+    st = Stats()
+    _check(lib().rwc_sample_trees(g, int(seed), int(tree0), int(num_trees),
+                                  _dptr(sums, torch.float64, "sums"),
+                                  _dptr(parents, torch.int32, "parents"),
+                                  _dptr(visits, torch.int32, "visits"),
+                                  ctypes.byref(opt) if opt is not None else None,
+                                  ctypes.byref(st), _stream(stream)))
+    return st
+
+
+def rwc_estimate(g, sums, num_trees, cg_tol, H_out, y_out=None, stream=None):
+    import torch
+    _check(lib().rwc_estimate(g, _dptr(sums, torch.float64, "sums"), int(num_trees),
+                              float(cg_tol), _dptr(H_out, torch.float64, "H_out"),
+                              _dptr(y_out, torch.float64, "y_out"), _stream(stream)))
+
+
+def rwc_recover(g, sums, num_trees, y, H_out, stream=None):
+    import torch
+    _check(lib().rwc_recover(g, _dptr(sums, torch.float64, "sums"), int(num_trees),
+                             _dptr(y, torch.float64, "y"), _dptr(H_out, torch.float64, "H_out"),
+                             _stream(stream)))
+
+
+def rwc_solve(g, k, B, X, tol, stream=None) -> int:
+    import torch
+    it = _i32(0)
+    _check(lib().rwc_solve(g, int(k), _dptr(B, torch.float64, "B"), _dptr(X, torch.float64, "X"),
+                           float(tol), ctypes.byref(it), _stream(stream)))
+    return it.value
+
+
+def rwc_grad(g, c, k, sketch_seed, cg_tol, grad_w, stream=None):
+    import torch
+    _check(lib().rwc_grad(g, _dptr(c, torch.float64, "c"), int(k), int(sketch_seed),
+                          float(cg_tol), _dptr(grad_w, torch.float32, "grad_w"), _stream(stream)))
+
+
+def rwc_batch_create(G, graph_offsets, row_ptr, col_idx, w=None):
+    go, pgo = _hptr(graph_offsets, np.int64)
+    rp, prp = _hptr(row_ptr, np.int64)
+    ci, pci = _hptr(col_idx, np.int32)
+    ww, pw = _hptr(w, np.float32)
+    out = _vp()
+    _check(lib().rwc_batch_create(int(G), pgo, prp, pci, pw, ctypes.byref(out)))
+    return out.value
+
+
+def rwc_batch_sample(b, seed, trees_per_graph, sums, use_graph=1, per_graph_launch=0,
+                     stream=None) -> Stats:
+    import torch
+    st = Stats()
+    _check(lib().rwc_batch_sample(b, int(seed), int(trees_per_graph),
+                                  _dptr(sums, torch.float64, "sums"), int(use_graph),
+                                  int(per_graph_launch), ctypes.byref(st), _stream(stream)))
+    return st
+
+
+def rwc_batch_roots(b, G) -> np.ndarray:
+    out = np.zeros(G, np.int32)
+    _check(lib().rwc_batch_roots(b, out.ctypes.data))
+    return out
+
+
+def rwc_autotune(b, cache_path=None, stream=None):
+    _check(lib().rwc_autotune(b, cache_path.encode() if cache_path else None, _stream(stream)))
+
+
+def rwc_batch_destroy(b):
+    _check(lib().rwc_batch_destroy(b))

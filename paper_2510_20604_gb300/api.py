@@ -1,0 +1,180 @@
+"""Convenience objects over the C ABI: graph/batch handles that free
+themselves, the FastWalk pipeline, and a torch.autograd.Function whose
+backward is the library's hand-written gradient.  All computation happens in
+librwc.so; this module only allocates torch buffers and forwards pointers."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _binding as B
+
+
+class Graph:
+    """Device copy of a connected undirected graph (CSR, both arc directions)."""
+
+    def __init__(self, row_ptr, col_idx, w=None, root=-1, flags=0):
+        row_ptr = np.ascontiguousarray(row_ptr, np.int64)
+        col_idx = np.ascontiguousarray(col_idx, np.int32)
+        self.row_ptr, self.col_idx = row_ptr, col_idx
+        self.w = None if w is None else np.ascontiguousarray(w, np.float32)
+        self.handle = B.rwc_graph_create(len(row_ptr) - 1, int(row_ptr[-1]), row_ptr, col_idx,
+                                         self.w, root, flags)
+        self.info = B.rwc_graph_info(self.handle)
+
+    @classmethod
+    def from_synth(cls, g, root=-1, flags=0):
+        return cls(g.row_ptr, g.col, g.w, root, flags)
+
+    n = property(lambda self: self.info.n)
+    nnz = property(lambda self: self.info.nnz)
+    root = property(lambda self: self.info.root)
+    vol = property(lambda self: self.info.vol)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            B.rwc_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sample(self, num_trees, seed=1, tree0=0, sums=None, want_trees=False, opt=None,
+               stream=None):
+        import torch
+        dev = torch.device("cuda")
+        if sums is None:
+            sums = torch.zeros(self.n, dtype=torch.float64, device=dev)
+        par = vis = None
+        if want_trees:
+            par = torch.empty((num_trees, self.n), dtype=torch.int32, device=dev)
+            vis = torch.empty((num_trees, self.n), dtype=torch.int32, device=dev)
+        st = B.rwc_sample_trees(self.handle, seed, tree0, num_trees, sums, par, vis, opt, stream)
+        return sums, st, par, vis
+
+    def estimate(self, sums, num_trees, tol=1e-10, want_y=False, stream=None):
+        import torch
+        H = torch.empty(self.n, dtype=torch.float64, device=sums.device)
+        y = torch.empty_like(H) if want_y else None
+        B.rwc_estimate(self.handle, sums, num_trees, tol, H, y, stream)
+        return (H, y) if want_y else H
+
+    def grad(self, c, k=64, sketch_seed=0, tol=1e-8, stream=None):
+        import torch
+        g = torch.empty(self.nnz // 2, dtype=torch.float32, device=c.device)
+        B.rwc_grad(self.handle, c, k, sketch_seed, tol, g, stream)
+        return g
+
+
+def fastwalk(graph: Graph, num_trees: int, seed: int = 1, tol: float = 1e-10, stream=None):
+    """Algorithm 3 (FastWalk) with a given tree count: sample, then AppRWC."""
+    sums, st, _, _ = graph.sample(num_trees, seed=seed, stream=stream)
+    return graph.estimate(sums, num_trees, tol=tol, stream=stream), st
+
+
+class Batch:
+    def __init__(self, graphs):
+        """graphs: sequence of objects with row_ptr, col, w (synth.Graph)."""
+        offs = [0]
+        rps, cols, ws = [], [], []
+        arc = 0
+        for g in graphs:
+            rps.append(np.asarray(g.row_ptr[:-1], np.int64) + arc)
+            cols.append(np.asarray(g.col, np.int32))
+            ws.append(g.w)
+            arc += int(g.row_ptr[-1])
+            offs.append(offs[-1] + g.n)
+        rps.append(np.array([arc], np.int64))
+        self.G = len(graphs)
+        self.offsets = np.array(offs, np.int64)
+        self.row_ptr = np.concatenate(rps)
+        self.col = np.concatenate(cols)
+        w = None if any(x is None for x in ws) else np.concatenate(ws).astype(np.float32)
+        self.handle = B.rwc_batch_create(self.G, self.offsets, self.row_ptr, self.col, w)
+        self.N = int(self.offsets[-1])
+
+    def roots(self):
+        return B.rwc_batch_roots(self.handle, self.G)
+
+    def sample(self, trees_per_graph, seed=1, sums=None, use_graph=1, per_graph_launch=0,
+               stream=None):
+        import torch
+        if sums is None:
+            sums = torch.zeros(self.N, dtype=torch.float64, device="cuda")
+        st = B.rwc_batch_sample(self.handle, seed, trees_per_graph, sums, use_graph,
+                                per_graph_launch, stream)
+        return sums, st
+
+    def autotune(self, cache_path=None, stream=None):
+        B.rwc_autotune(self.handle, cache_path, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            B.rwc_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _edge_index(row_ptr, col):
+    """For every arc, the index of its undirected edge in (a < b) CSR order."""
+    n = len(row_ptr) - 1
+    src = np.repeat(np.arange(n, dtype=np.int64), np.diff(row_ptr))
+    dst = col.astype(np.int64)
+    up = src < dst
+    eid = np.full(len(col), -1, np.int64)
+    eid[up] = np.arange(int(up.sum()))
+    keys_up = src[up] * n + dst[up]
+    order = np.argsort(keys_up, kind="stable")
+    lo_keys = dst[~up] * n + src[~up]
+    pos = np.searchsorted(keys_up[order], lo_keys, side="left")
+    eid[~up] = np.arange(int(up.sum()))[order][pos]
+    return eid
+
+
+def _make_function():
+    import torch
+
+    class RWCFunction(torch.autograd.Function):
+        """H = FastWalk estimate of the random walk centrality for edge weights
+        w (one per undirected edge, (a < b) CSR order).  backward returns the
+        gradient of the exact centrality, sum_v g_v dH_v/dw, computed by the
+        library (rwc_grad) with a JL sketch of size k (k = 0: exact)."""
+
+        @staticmethod
+        def forward(ctx, w, row_ptr, col_idx, num_trees, seed, k, sketch_seed):
+            eid = _edge_index(row_ptr, col_idx)
+            warc = w.detach().double().cpu().numpy()[eid].astype(np.float32)
+            g = Graph(row_ptr, col_idx, warc)
+            H, _ = fastwalk(g, num_trees, seed)
+            ctx.g, ctx.k, ctx.sketch_seed = g, k, sketch_seed
+            return H.to(w.dtype)
+
+        @staticmethod
+        def backward(ctx, gout):
+            c = gout.detach().double().contiguous()
+            pos, neg = c.clamp(min=0), (-c).clamp(min=0)
+            grad = ctx.g.grad(pos.contiguous(), ctx.k, ctx.sketch_seed).double()
+            if bool((neg > 0).any()):
+                grad = grad - ctx.g.grad(neg.contiguous(), ctx.k, ctx.sketch_seed).double()
+            return grad.to(gout.dtype), None, None, None, None, None, None
+
+    return RWCFunction
+
+
+class _Lazy:
+    _cls = None
+
+    def __getattr__(self, name):
+        if _Lazy._cls is None:
+            _Lazy._cls = _make_function()
+        return getattr(_Lazy._cls, name)
+
+
+RWCFunction = _Lazy()

@@ -1,0 +1,465 @@
+// Batched sampler: all trees of thousands of small graphs in one persistent
+// launch per size class, work items (graph, tile of trees) pulled from a
+// device counter (no grid-wide barrier); the launches of a call are captured
+// once into a CUDA graph and replayed.  Each tree runs in one thread block
+// with its state in shared memory (smem_tree.cuh).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rwc_common.cuh"
+#include "smem_tree.cuh"
+
+namespace rwc {
+namespace {
+
+struct BGraph {
+    int64_t voff;   // first vertex in the concatenated arrays
+    int32_t n;
+    int32_t root;
+};
+
+struct BItem {
+    int32_t g;
+    int32_t tile;   // index of the tile of trees within the graph
+};
+
+constexpr int NCLASS = 2;
+
+template <bool OFF64, bool W>
+__global__ void b_persistent(DevGraph base, const BGraph *__restrict__ graphs,
+                             const BItem *__restrict__ items, int64_t nitems, int *next_item,
+                             int tile, int64_t T, uint32_t k0, uint32_t k1, int64_t max_rounds,
+                             double *sums, int *err, unsigned long long *round_ctr) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int item;
+    unsigned long long rounds_here = 0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) item = atomicAdd(next_item, 1);
+        __syncthreads();
+        const int i = item;
+        if (i >= nitems) break;
+        const BItem it = items[i];
+        const BGraph bg = graphs[it.g];
+        DevGraph g = base;
+        g.n = bg.n;
+        g.root = bg.root;
+        if (OFF64) g.rp64 = base.rp64 + bg.voff;
+        else g.rp32 = base.rp32 + bg.voff;
+        SmemTree S;
+        S.carve(smem, bg.n);
+        for (int u = threadIdx.x; u < bg.n; u += blockDim.x) S.acc[u] = 0;
+        const int64_t t0 = (int64_t)it.tile * tile, t1 = std::min<int64_t>(T, t0 + tile);
+        int mask = 0;
+        for (int64_t t = t0; t < t1 && !mask; ++t) {
+            int64_t r = 0;
+            mask = smem_tree<OFF64, W>(g, S, (uint32_t)t, (uint32_t)it.g, k0, k1, max_rounds,
+                                       nullptr, nullptr, &r);
+            rounds_here += (unsigned long long)r;
+        }
+        __syncthreads();
+        if (mask) { if (threadIdx.x == 0) atomicOr(err, mask); break; }
+        unsigned long long draws = 0;
+        for (int u = threadIdx.x; u < bg.n; u += blockDim.x) {
+            draws += S.acc[u];
+            if (S.acc[u]) atomicAdd(sums + bg.voff + u, (double)S.acc[u]);
+        }
+        if (draws) atomicAdd(round_ctr + 1, draws);
+    }
+    if (threadIdx.x == 0 && rounds_here) atomicAdd(round_ctr, rounds_here);
+}
+
+template <class F>
+void dispatch(bool off64, bool weighted, F f) {
+    if (off64) {
+        if (weighted) f(std::true_type{}, std::true_type{});
+        else f(std::true_type{}, std::false_type{});
+    } else {
+        if (weighted) f(std::false_type{}, std::true_type{});
+        else f(std::false_type{}, std::false_type{});
+    }
+}
+
+}  // namespace
+}  // namespace rwc
+
+using namespace rwc;
+
+struct rwc_batch {
+    int32_t G = 0;
+    int64_t N = 0, nnz = 0;
+    bool off64 = false, weighted = false;
+    std::vector<BGraph> hgraphs;
+    std::vector<int32_t> roots;
+    DevGraph base;                     // concatenated CSR (local column ids)
+    BGraph *graphs = nullptr;
+    // size classes: [0] n <= class_split, [1] the rest
+    int class_split = 2048;
+    int threads[NCLASS] = {256, 512};
+    int tile = 4;
+    int max_n[NCLASS] = {0, 0};
+    BItem *items[NCLASS] = {nullptr, nullptr};
+    int64_t nitems[NCLASS] = {0, 0};
+    int64_t items_T = -1;              // T the item lists were built for
+    int64_t items_tile = -1;
+    void *scratch = nullptr;           // [0] err, [8] rounds, [16] draws, [32..96) item counters
+    std::vector<void *> allocs;
+    // captured launches
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t cap_seed = 0;
+    int64_t cap_T = -1;
+    double *cap_sums = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int64_t *host = nullptr;
+};
+
+namespace {
+
+cudaError_t balloc(rwc_batch *b, void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e == cudaSuccess) b->allocs.push_back(*p);
+    return e;
+}
+
+void drop_graph(rwc_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->cap_T = -1;
+}
+
+// Work items of each size class for T trees per graph, largest graphs first.
+rwc_status build_items(rwc_batch *b, int64_t T) {
+    if (b->items_T == T && b->items_tile == b->tile) return RWC_OK;
+    for (int c = 0; c < NCLASS; ++c) {
+        std::vector<BItem> v;
+        std::vector<int32_t> order;
+        for (int32_t g = 0; g < b->G; ++g) {
+            const int cls = b->hgraphs[g].n <= b->class_split ? 0 : 1;
+            if (cls == c) order.push_back(g);
+        }
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int32_t x, int32_t y) { return b->hgraphs[x].n > b->hgraphs[y].n; });
+        const int64_t ntile = (T + b->tile - 1) / b->tile;
+        for (int64_t t = 0; t < ntile; ++t)
+            for (int32_t g : order) v.push_back(BItem{g, (int32_t)t});
+        // largest graphs' tiles first overall
+        std::stable_sort(v.begin(), v.end(), [&](const BItem &x, const BItem &y) {
+            return b->hgraphs[x.g].n > b->hgraphs[y.g].n;
+        });
+        if (b->items[c]) { cudaFree(b->items[c]); b->allocs.erase(std::find(b->allocs.begin(), b->allocs.end(), (void *)b->items[c])); }
+        b->items[c] = nullptr;
+        b->nitems[c] = (int64_t)v.size();
+        if (!v.empty()) {
+            RWC_CUDA_TRY(balloc(b, (void **)&b->items[c], v.size() * sizeof(BItem)));
+            RWC_CUDA_TRY(cudaMemcpy(b->items[c], v.data(), v.size() * sizeof(BItem), cudaMemcpyHostToDevice));
+        }
+        b->max_n[c] = 0;
+        for (int32_t g : order) b->max_n[c] = std::max(b->max_n[c], b->hgraphs[g].n);
+    }
+    b->items_T = T;
+    b->items_tile = b->tile;
+    drop_graph(b);
+    return RWC_OK;
+}
+
+// Enqueue the persistent launches of one call.
+rwc_status enqueue(rwc_batch *b, uint64_t seed, int64_t T, double *sums, cudaStream_t st) {
+    int *err = (int *)b->scratch;
+    unsigned long long *rounds = (unsigned long long *)((char *)b->scratch + 8);
+    int *counters = (int *)((char *)b->scratch + 32);
+    RWC_CUDA_TRY(cudaMemsetAsync((char *)b->scratch + 32, 0, 64, st));
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    rwc_status status = RWC_OK;
+    for (int c = 0; c < NCLASS; ++c) {
+        if (!b->nitems[c]) continue;
+        const size_t smem = smem_tree_bytes(b->max_n[c]);
+        dispatch(b->off64, b->weighted, [&](auto o64, auto wt) {
+            auto kern = b_persistent<decltype(o64)::value, decltype(wt)::value>;
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, b->threads[c], smem);
+            if (per_sm < 1) { status = set_error(RWC_ERR_UNSUPPORTED, "batch class %d does not fit on an SM", c); return; }
+            const int64_t blocks = std::min<int64_t>(b->nitems[c], (int64_t)num_sms() * per_sm);
+            ::rwc::count_launches(1); kern<<<(unsigned)blocks, b->threads[c], smem, st>>>(
+                b->base, b->graphs, b->items[c], b->nitems[c], counters + c, b->tile, T, k0, k1,
+                (int64_t)1 << 22, sums, err, rounds);
+        });
+        RWC_TRY(status);
+        RWC_CUDA_TRY(cudaGetLastError());
+    }
+    return RWC_OK;
+}
+
+rwc_status finish(rwc_batch *b, rwc_stats_t *stats, int mode, int64_t T, cudaStream_t st) {
+    RWC_CUDA_TRY(cudaMemcpyAsync(b->host, b->scratch, 24, cudaMemcpyDeviceToHost, st));
+    RWC_CUDA_TRY(cudaStreamSynchronize(st));
+    const int e = (int)(b->host[0] & 0xffffffff);
+    if (e & SM_ERR_KOVF) return set_error(RWC_ERR_UNSUPPORTED, "a vertex was popped more than 65535 times");
+    if (e & SM_ERR_LOOP) return set_error(RWC_ERR_CUDA, "sampler internal check failed");
+    if (e) return set_error(RWC_ERR_NOT_CONVERGED, "cycle popping exceeded max_rounds");
+    if (stats) {
+        stats->trees = T * b->G;
+        stats->rounds = b->host[1];
+        stats->draws = b->host[2];
+        stats->marked = b->host[2];
+        stats->chunks = 1;
+        stats->mode = mode;
+    }
+    return RWC_OK;
+}
+
+}  // namespace
+
+extern "C" rwc_status rwc_batch_create(int32_t G, const int64_t *voff, const int64_t *rp,
+                                       const int32_t *col, const float *w, rwc_batch_t **out) {
+    clear_error();
+    if (!out || G <= 0 || !voff || !rp || !col) return set_error(RWC_ERR_INVALID, "bad argument");
+    *out = nullptr;
+    if (voff[0] != 0) return set_error(RWC_ERR_INVALID, "graph offsets must start at 0");
+    const int64_t N = voff[G];
+    const int64_t nnz = rp[N];
+    if (rp[0] != 0) return set_error(RWC_ERR_INVALID, "row_ptr[0] must be 0");
+    std::vector<BGraph> hg(G);
+    std::vector<int32_t> roots(G);
+    std::vector<int64_t> lrp;
+    for (int32_t g = 0; g < G; ++g) {
+        const int64_t v0 = voff[g], n = voff[g + 1] - v0;
+        if (n < 2 || n > 20000) return set_error(RWC_ERR_INVALID, "graph %d: batch graphs need 2 <= n <= 20000", g);
+        lrp.resize(n + 1);
+        for (int64_t u = 0; u <= n; ++u) lrp[u] = rp[v0 + u] - rp[v0];
+        const int32_t *gc = col + rp[v0];
+        const float *gw = w ? w + rp[v0] : nullptr;
+        rwc_status s = validate_csr(n, lrp[n], lrp.data(), gc, gw);
+        if (s != RWC_OK) return set_error(s, "graph %d: %s", g, rwc_last_error());
+        if (!csr_connected(n, lrp.data(), gc)) return set_error(RWC_ERR_NOT_CONNECTED, "graph %d is not connected", g);
+        double best = -1.0;
+        int32_t arg = 0;
+        for (int64_t u = 0; u < n; ++u) {
+            double d = 0.0;
+            if (gw) for (int64_t j = lrp[u]; j < lrp[u + 1]; ++j) d = d + (double)gw[j - 0];
+            else d = (double)(lrp[u + 1] - lrp[u]);
+            if (d > best) { best = d; arg = (int32_t)u; }
+        }
+        hg[g] = BGraph{v0, (int32_t)n, arg};
+        roots[g] = arg;
+    }
+    rwc_batch *b = new (std::nothrow) rwc_batch();
+    if (!b) return set_error(RWC_ERR_OOM, "host allocation failed");
+    auto fail = [&](cudaError_t e) {
+        for (void *p : b->allocs) cudaFree(p);
+        if (b->host) cudaFreeHost(b->host);
+        delete b;
+        return set_error(e == cudaErrorMemoryAllocation ? RWC_ERR_OOM : RWC_ERR_CUDA, "batch upload: %s",
+                         cudaGetErrorString(e));
+    };
+    b->G = G; b->N = N; b->nnz = nnz; b->hgraphs = hg; b->roots = roots;
+    b->weighted = (w != nullptr);
+    b->off64 = nnz >= ((int64_t)1 << 31) - 1;
+    cudaError_t e;
+    DevGraph &d = b->base;
+    d.n = N; d.nnz = nnz; d.weighted = b->weighted; d.off64 = b->off64;
+    if (b->off64) {
+        int64_t *p;
+        if ((e = balloc(b, (void **)&p, (N + 1) * 8)) != cudaSuccess) return fail(e);
+        if ((e = cudaMemcpy(p, rp, (N + 1) * 8, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+        d.rp64 = p;
+    } else {
+        std::vector<int32_t> r32(N + 1);
+        for (int64_t i = 0; i <= N; ++i) r32[i] = (int32_t)rp[i];
+        int32_t *p;
+        if ((e = balloc(b, (void **)&p, (N + 1) * 4)) != cudaSuccess) return fail(e);
+        if ((e = cudaMemcpy(p, r32.data(), (N + 1) * 4, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+        d.rp32 = p;
+    }
+    {
+        int32_t *p;
+        if ((e = balloc(b, (void **)&p, nnz * 4)) != cudaSuccess) return fail(e);
+        if ((e = cudaMemcpy(p, col, nnz * 4, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+        d.col = p;
+    }
+    if (w) {
+        std::vector<WArc> arcs(nnz);
+        std::vector<double> prob;
+        std::vector<int64_t> ql, qh;
+        std::vector<uint32_t> thr;
+        std::vector<int32_t> al;
+        for (int64_t u = 0; u < N; ++u) {
+            const int64_t b0 = rp[u], deg = rp[u + 1] - rp[u];
+            thr.resize(deg); al.resize(deg);
+            vose_row(w + b0, deg, thr.data(), al.data(), prob, ql, qh);
+            for (int64_t j = 0; j < deg; ++j) arcs[b0 + j] = WArc{col[b0 + j], thr[j], col[b0 + al[j]], al[j]};
+        }
+        WArc *p;
+        if ((e = balloc(b, (void **)&p, nnz * sizeof(WArc))) != cudaSuccess) return fail(e);
+        if ((e = cudaMemcpy(p, arcs.data(), nnz * sizeof(WArc), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+        d.warc = p;
+    }
+    if ((e = balloc(b, (void **)&b->graphs, G * sizeof(BGraph))) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(b->graphs, hg.data(), G * sizeof(BGraph), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
+    if ((e = balloc(b, &b->scratch, 128)) != cudaSuccess) return fail(e);
+    if ((e = cudaMallocHost((void **)&b->host, 64)) != cudaSuccess) return fail(e);
+    *out = b;
+    return RWC_OK;
+}
+
+extern "C" rwc_status rwc_batch_roots(const rwc_batch_t *b, int32_t *host_roots) {
+    if (!b || !host_roots) return set_error(RWC_ERR_INVALID, "bad argument");
+    memcpy(host_roots, b->roots.data(), b->roots.size() * sizeof(int32_t));
+    return RWC_OK;
+}
+
+extern "C" rwc_status rwc_batch_sample(rwc_batch_t *b, uint64_t seed, int64_t T, double *sums,
+                                       int32_t use_graph, int32_t per_graph_launch,
+                                       rwc_stats_t *stats, rwc_stream_t stream) {
+    clear_error();
+    if (!b || !sums || T <= 0 || T > ((int64_t)1 << 31)) return set_error(RWC_ERR_INVALID, "bad argument");
+    if (stats) memset(stats, 0, sizeof(*stats));
+    cudaStream_t st = (cudaStream_t)stream;
+    RWC_CUDA_TRY(cudaMemsetAsync(b->scratch, 0, 32, st));
+    if (per_graph_launch) {
+        // baseline: one launch per graph, same per-tree kernel
+        int *err = (int *)b->scratch;
+        unsigned long long *rounds = (unsigned long long *)((char *)b->scratch + 8);
+        const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+        for (int32_t g = 0; g < b->G; ++g) {
+            const BGraph &bg = b->hgraphs[g];
+            DevGraph dg = b->base;
+            dg.n = bg.n; dg.root = bg.root;
+            if (b->off64) dg.rp64 = b->base.rp64 + bg.voff; else dg.rp32 = b->base.rp32 + bg.voff;
+            const int thr = bg.n <= b->class_split ? b->threads[0] : b->threads[1];
+            const size_t smem = smem_tree_bytes(bg.n);
+            rwc_status status = RWC_OK;
+            dispatch(b->off64, b->weighted, [&](auto o64, auto wt) {
+                auto kern = s_trees<decltype(o64)::value, decltype(wt)::value>;
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                int per_sm = 0;
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, thr, smem);
+                if (per_sm < 1) { status = set_error(RWC_ERR_UNSUPPORTED, "graph %d does not fit", g); return; }
+                const int64_t blocks = std::min<int64_t>(T, (int64_t)num_sms() * per_sm);
+                ::rwc::count_launches(1); kern<<<(unsigned)blocks, thr, smem, st>>>(dg, 0u, T, k0, k1, (uint32_t)g, (int64_t)1 << 22,
+                                                           sums + bg.voff, nullptr, nullptr, err, rounds);
+            });
+            RWC_TRY(status);
+        }
+        RWC_CUDA_TRY(cudaGetLastError());
+        return finish(b, stats, 3, T, st);
+    }
+    RWC_TRY(build_items(b, T));
+    if (!use_graph) {
+        RWC_TRY(enqueue(b, seed, T, sums, st));
+        return finish(b, stats, 4, T, st);
+    }
+    if (!b->exec || b->cap_seed != seed || b->cap_T != T || b->cap_sums != sums || b->cap_stream != st) {
+        drop_graph(b);
+        cudaStream_t cs;
+        RWC_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        rwc_status s = RWC_OK;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            s = enqueue(b, seed, T, sums, cs);
+            cudaGraph_t gr = nullptr;
+            e = cudaStreamEndCapture(cs, &gr);
+            if (s == RWC_OK && e == cudaSuccess) {
+                b->graph = gr;
+                e = cudaGraphInstantiate(&b->exec, gr, 0);
+            } else if (gr) {
+                cudaGraphDestroy(gr);
+            }
+        }
+        cudaStreamDestroy(cs);
+        RWC_TRY(s);
+        if (e != cudaSuccess) { drop_graph(b); return set_error(RWC_ERR_CUDA, "CUDA graph capture: %s", cudaGetErrorString(e)); }
+        b->cap_seed = seed; b->cap_T = T; b->cap_sums = sums; b->cap_stream = st;
+    }
+    RWC_CUDA_TRY(cudaGraphLaunch(b->exec, st));
+    return finish(b, stats, 5, T, st);
+}
+
+extern "C" rwc_status rwc_autotune(rwc_batch_t *b, const char *cache_path, rwc_stream_t stream) {
+    clear_error();
+    if (!b) return set_error(RWC_ERR_INVALID, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    char sig[128];
+    snprintf(sig, sizeof(sig), "G%d_N%lld_E%lld", b->G, (long long)b->N, (long long)b->nnz);
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "r");
+        if (f) {
+            char buf[4096];
+            size_t len = fread(buf, 1, sizeof(buf) - 1, f);
+            fclose(f);
+            buf[len] = 0;
+            const char *p = strstr(buf, sig);
+            int t0, t1, tl, cs;
+            if (p && sscanf(strchr(p, ':') + 1, " [%d, %d, %d, %d]", &t0, &t1, &tl, &cs) == 4) {
+                b->threads[0] = t0; b->threads[1] = t1; b->tile = tl; b->class_split = cs;
+                b->items_T = -1;
+                return RWC_OK;
+            }
+        }
+    }
+    double *sums = nullptr;
+    RWC_CUDA_TRY(cudaMallocAsync((void **)&sums, b->N * sizeof(double), st));
+    const int cand0[] = {128, 256, 512};
+    const int cand1[] = {256, 512, 1024};
+    const int tiles[] = {1, 4, 16};
+    const int splits[] = {1024, 2048, 4096};
+    const int64_t Tp = 16;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bt0 = b->threads[0], bt1 = b->threads[1], btl = b->tile, bcs = b->class_split;
+    rwc_status status = RWC_OK;
+    for (int cs : splits)
+        for (int t0 : cand0)
+            for (int t1 : cand1)
+                for (int tl : tiles) {
+                    b->threads[0] = t0; b->threads[1] = t1; b->tile = tl; b->class_split = cs;
+                    b->items_T = -1;
+                    if ((status = build_items(b, Tp)) != RWC_OK) goto done;
+                    cudaMemsetAsync(b->scratch, 0, 32, st);
+                    if ((status = enqueue(b, 12345, Tp, sums, st)) != RWC_OK) { status = RWC_OK; continue; }
+                    cudaEventRecord(e0, st);
+                    cudaMemsetAsync(b->scratch, 0, 32, st);
+                    if ((status = enqueue(b, 12346, Tp, sums, st)) != RWC_OK) { status = RWC_OK; continue; }
+                    cudaEventRecord(e1, st);
+                    cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best) { best = ms; bt0 = t0; bt1 = t1; btl = tl; bcs = cs; }
+                }
+done:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(sums, st);
+    RWC_CUDA_TRY(cudaStreamSynchronize(st));
+    RWC_TRY(status);
+    b->threads[0] = bt0; b->threads[1] = bt1; b->tile = btl; b->class_split = bcs;
+    b->items_T = -1;
+    drop_graph(b);
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "w");
+        if (f) {
+            fprintf(f, "{\"%s\": [%d, %d, %d, %d]}\n", sig, bt0, bt1, btl, bcs);
+            fclose(f);
+        }
+    }
+    return RWC_OK;
+}
+
+extern "C" rwc_status rwc_batch_destroy(rwc_batch_t *b) {
+    if (!b) return RWC_OK;
+    drop_graph(b);
+    for (void *p : b->allocs) cudaFree(p);
+    if (b->host) cudaFreeHost(b->host);
+    delete b;
+    return RWC_OK;
+}

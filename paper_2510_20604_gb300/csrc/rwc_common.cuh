@@ -1,0 +1,159 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "rwc.h"
+
+namespace rwc {
+
+// ------------------------------------------------------------ error model
+rwc_status set_error(rwc_status st, const char *fmt, ...);
+void clear_error();
+
+#define RWC_CUDA_TRY(expr)                                                    \
+    do {                                                                      \
+        cudaError_t e_ = (expr);                                              \
+        if (e_ != cudaSuccess) {                                              \
+            return ::rwc::set_error(e_ == cudaErrorMemoryAllocation ? RWC_ERR_OOM \
+                                                                    : RWC_ERR_CUDA, \
+                                    "%s failed: %s (%s:%d)", #expr,           \
+                                    cudaGetErrorString(e_), __FILE__, __LINE__); \
+        }                                                                     \
+    } while (0)
+
+#define RWC_TRY(expr)                                                         \
+    do {                                                                      \
+        rwc_status s_ = (expr);                                               \
+        if (s_ != RWC_OK) return s_;                                          \
+    } while (0)
+
+// ----------------------------------------------------------- device graph
+// Arc record of a weighted graph: the arc's head, its alias threshold and
+// the head of its alias arc, so that one 16-byte load resolves a weighted
+// neighbour pick.
+struct __align__(16) WArc {
+    int32_t col;
+    uint32_t thr;
+    int32_t alias_col;
+    int32_t alias_idx;
+};
+
+struct DevGraph {
+    int64_t n = 0, nnz = 0;
+    int32_t root = 0;
+    bool weighted = false;
+    bool off64 = false;
+    const int32_t *rp32 = nullptr;   // [n+1] when !off64
+    const int64_t *rp64 = nullptr;   // [n+1] when off64
+    const int32_t *col = nullptr;    // [nnz] arc heads
+    const WArc *warc = nullptr;      // [nnz] when weighted
+    const float *w = nullptr;        // [nnz] when weighted (solver)
+    const double *d = nullptr;       // [n] weighted degrees
+    const float *dinv32 = nullptr;   // [n] 1/d (Jacobi preconditioner)
+    double vol = 0.0, dmax = 0.0;
+};
+
+}  // namespace rwc
+
+struct rwc_graph {
+    rwc::DevGraph g;
+    int64_t device_bytes = 0;
+    void *allocs[16] = {};
+    int nallocs = 0;
+    // pinned host scalars used by synchronising entry points
+    int64_t *host_scalars = nullptr;
+};
+
+namespace rwc {
+
+cudaError_t graph_alloc(rwc_graph *G, void **p, size_t bytes);
+
+// Host-side CSR checks (graph.cu): see rwc_graph_create for the rules.
+rwc_status validate_csr(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *col,
+                        const float *w);
+bool csr_connected(int64_t n, const int64_t *rp, const int32_t *col);
+// Vose alias table of one row (graph.cu), scratch vectors supplied by caller.
+void vose_row(const float *w, int64_t deg, uint32_t *thr, int32_t *alias,
+              std::vector<double> &prob, std::vector<int64_t> &lo_q, std::vector<int64_t> &hi_q);
+
+// X = L^+ B for node-major [n][k] FP64 arrays (solver.cu).
+rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, double tol,
+                           int *iters_out, cudaStream_t st);
+
+// --------------------------------------------------------------- Philox
+// Philox-4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11): each round
+// multiplies words 0 and 2 by the two Philox constants, and mixes the high
+// halves into words 1 and 3 with the round key; the key advances by the two
+// Weyl constants between rounds.
+struct Ctr4 { uint32_t x, y, z, w; };
+
+__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+    return __umulhi(a, b);
+#else
+    return (uint32_t)(((uint64_t)a * (uint64_t)b) >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ Ctr4 philox4x32_10(Ctr4 c, uint32_t k0, uint32_t k1) {
+    const uint32_t A = 0xD2511F53u, B = 0xCD9E8D57u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hA = mulhi32(A, c.x), lA = A * c.x;
+        const uint32_t hB = mulhi32(B, c.z), lB = B * c.z;
+        c = Ctr4{hB ^ c.y ^ k0, lB, hA ^ c.w ^ k1, lA};
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Row bounds of vertex u.
+template <bool OFF64>
+__device__ __forceinline__ void row_bounds(const DevGraph &g, int32_t u, int64_t &b, uint32_t &deg) {
+    if (OFF64) {
+        const int64_t b0 = __ldg(g.rp64 + u), b1 = __ldg(g.rp64 + u + 1);
+        b = b0; deg = (uint32_t)(b1 - b0);
+    } else {
+        const int32_t b0 = __ldg(g.rp32 + u), b1 = __ldg(g.rp32 + u + 1);
+        b = b0; deg = (uint32_t)(b1 - b0);
+    }
+}
+
+// The c-th successor-stack entry of vertex u in tree `tree` of graph `gid`:
+// the neighbour returned by the c-th call of RandomNeighbor(u) (Algorithm 3).
+template <bool OFF64, bool WEIGHTED>
+__device__ __forceinline__ int32_t succ(const DevGraph &g, int32_t u, uint32_t c, uint32_t tree,
+                                        uint32_t gid, uint32_t k0, uint32_t k1) {
+    int64_t b; uint32_t deg;
+    row_bounds<OFF64>(g, u, b, deg);
+    const Ctr4 o = philox4x32_10(Ctr4{c, (uint32_t)u, tree, gid}, k0, k1);
+    const uint32_t j = __umulhi(o.x, deg);
+    if (WEIGHTED) {
+        const WArc a = g.warc[b + j];
+        return (o.y < a.thr) ? a.col : a.alias_col;
+    } else {
+        return __ldg(g.col + b + j);
+    }
+}
+
+// ------------------------------------------------------------- helpers
+// Library-wide kernel launch counter (graph.cu).
+void count_launches(int64_t k);
+
+inline int num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+}  // namespace rwc

@@ -1,0 +1,398 @@
+// Laplacian solves, Algorithm 1 (AppRWC) and the centrality gradient.
+//
+// LapSolve (Lemma 3.2 names no concrete solver): X = L^+ B for k right-hand
+// sides.  Outer loop in FP64: R = B - L X (FP64 SpMV over the FP32 weights),
+// columns projected onto 1-perp; inner loop: Jacobi-preconditioned conjugate
+// gradients on the k columns together (one shared FP32 SpMM per iteration,
+// per-column step sizes, FP64 dot products), X += correction.  The matrix is
+// read once per iteration for all k columns; node-major [n][k] layout keeps
+// each gathered neighbour row contiguous.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "rwc_common.cuh"
+
+namespace rwc {
+namespace {
+
+constexpr int TPB = 256;
+
+struct Buf {
+    void *p = nullptr;
+    cudaStream_t st;
+    explicit Buf(cudaStream_t s) : st(s) {}
+    ~Buf() { if (p) cudaFreeAsync(p, st); }
+};
+
+template <bool OFF64>
+__device__ __forceinline__ void rowb(const DevGraph &g, int64_t u, int64_t &b, int64_t &e) {
+    if (OFF64) { b = g.rp64[u]; e = g.rp64[u + 1]; }
+    else { b = g.rp32[u]; e = g.rp32[u + 1]; }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Q = L P (FP32), node-major [n][k], one warp per row; also accumulates the
+// per-column dots pq[c] += sum_u P[u][c] Q[u][c] (FP64).
+template <bool OFF64, bool W>
+__global__ void __launch_bounds__(TPB) spmm32(DevGraph g, int k, const float *__restrict__ P,
+                                              float *__restrict__ Q, double *pq) {
+    extern __shared__ double sdot[];
+    for (int c = threadIdx.x; c < k; c += blockDim.x) sdot[c] = 0.0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = warp; u < g.n; u += nwarps) {
+        int64_t b, e;
+        rowb<OFF64>(g, u, b, e);
+        const float du = (float)g.d[u];
+        if (k == 1) {
+            float s = 0.f;
+            for (int64_t j = b + lane; j < e; j += 32) {
+                const float wj = W ? g.w[j] : 1.f;
+                s += wj * P[g.col[j]];
+            }
+            s = warp_sumf(s);
+            if (lane == 0) {
+                const float pu = P[u];
+                const float q = du * pu - s;
+                Q[u] = q;
+                atomicAdd(&sdot[0], (double)pu * (double)q);
+            }
+        } else {
+            for (int c0 = 0; c0 < k; c0 += 32) {
+                const int c = c0 + lane;
+                float s = 0.f;
+                if (c < k)
+                    for (int64_t j = b; j < e; ++j) {
+                        const float wj = W ? g.w[j] : 1.f;
+                        s += wj * P[(int64_t)g.col[j] * k + c];
+                    }
+                if (c < k) {
+                    const float pu = P[u * k + c];
+                    const float q = du * pu - s;
+                    Q[u * k + c] = q;
+                    atomicAdd(&sdot[c], (double)pu * (double)q);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < k; c += blockDim.x)
+        if (sdot[c] != 0.0) atomicAdd(&pq[c], sdot[c]);
+}
+
+// R = B - L X in FP64 (node-major), and the column sums of R.
+template <bool OFF64, bool W>
+__global__ void __launch_bounds__(TPB) resid64(DevGraph g, int k, const double *__restrict__ B,
+                                               const double *__restrict__ X, double *__restrict__ R,
+                                               double *colsum) {
+    extern __shared__ double ssum[];
+    for (int c = threadIdx.x; c < k; c += blockDim.x) ssum[c] = 0.0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = warp; u < g.n; u += nwarps) {
+        int64_t b, e;
+        rowb<OFF64>(g, u, b, e);
+        const double du = g.d[u];
+        if (k == 1) {
+            double s = 0.0;
+            for (int64_t j = b + lane; j < e; j += 32) {
+                const double wj = W ? (double)g.w[j] : 1.0;
+                s += wj * X[g.col[j]];
+            }
+            s = warp_sum(s);
+            if (lane == 0) {
+                const double r = B[u] - (du * X[u] - s);
+                R[u] = r;
+                atomicAdd(&ssum[0], r);
+            }
+        } else {
+            for (int c0 = 0; c0 < k; c0 += 32) {
+                const int c = c0 + lane;
+                if (c >= k) continue;
+                double s = 0.0;
+                for (int64_t j = b; j < e; ++j) {
+                    const double wj = W ? (double)g.w[j] : 1.0;
+                    s += wj * X[(int64_t)g.col[j] * k + c];
+                }
+                const double r = B[u * k + c] - (du * X[u * k + c] - s);
+                R[u * k + c] = r;
+                atomicAdd(&ssum[c], r);
+            }
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < k; c += blockDim.x)
+        if (ssum[c] != 0.0) atomicAdd(&colsum[c], ssum[c]);
+}
+
+// Per-column accumulation into shared memory: k == 1 sums in a register and
+// reduces once per warp; k > 1 adds element-wise (lanes hit distinct columns).
+struct ColAcc {
+    double *sh;
+    int k;
+    double reg = 0.0;
+    __device__ ColAcc(double *s, int kk) : sh(s), k(kk) {}
+    __device__ __forceinline__ void add(int c, double v) {
+        if (k == 1) reg += v;
+        else atomicAdd(&sh[c], v);
+    }
+    __device__ __forceinline__ void flush() {
+        if (k == 1) {
+            const double t = warp_sum(reg);
+            if ((threadIdx.x & 31) == 0 && t != 0.0) atomicAdd(&sh[0], t);
+        }
+    }
+};
+
+__device__ __forceinline__ void sh_zero(double *s, int k) {
+    for (int c = threadIdx.x; c < k; c += blockDim.x) s[c] = 0.0;
+    __syncthreads();
+}
+__device__ __forceinline__ void sh_flush(const double *s, int k, double *dst) {
+    __syncthreads();
+    for (int c = threadIdx.x; c < k; c += blockDim.x)
+        if (s[c] != 0.0) atomicAdd(&dst[c], s[c]);
+}
+
+// V[u][c] -= mean_c (FP64) and nrm[c] += V^2.
+__global__ void center64(int64_t n, int k, double *V, const double *colsum, double *nrm) {
+    extern __shared__ double sn[];
+    sh_zero(sn, k);
+    ColAcc acc(sn, k);
+    const int64_t tot = n * k;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % k);
+        const double v = V[i] - colsum[c] / (double)n;
+        V[i] = v;
+        acc.add(c, v * v);
+    }
+    acc.flush();
+    sh_flush(sn, k, nrm);
+}
+
+__global__ void colsum64(int64_t n, int k, const double *V, double *colsum) {
+    extern __shared__ double sn[];
+    sh_zero(sn, k);
+    ColAcc acc(sn, k);
+    const int64_t tot = n * k;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
+         i += (int64_t)gridDim.x * blockDim.x)
+        acc.add((int)(i % k), V[i]);
+    acc.flush();
+    sh_flush(sn, k, colsum);
+}
+
+// Start of an inner solve: r = R / |R_c| (FP32), e = 0, z = D^-1 r, p = z,
+// rz0[c] = <r, z>.
+__global__ void inner_start(int64_t n, int k, const double *R, const double *rnrm2,
+                            const float *dinv, float *r, float *e, float *z, float *p,
+                            double *rz0) {
+    extern __shared__ double s[];
+    sh_zero(s, k);
+    ColAcc acc(s, k);
+    const int64_t tot = n * k;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % k);
+        const int64_t u = i / k;
+        const double nr = sqrt(rnrm2[c]);
+        const float rv = nr > 0 ? (float)(R[i] / nr) : 0.f;
+        const float zv = dinv[u] * rv;
+        r[i] = rv; e[i] = 0.f; z[i] = zv; p[i] = zv;
+        acc.add(c, (double)rv * (double)zv);
+    }
+    acc.flush();
+    sh_flush(s, k, rz0);
+}
+
+// alpha_c = rz[c] / pq[c]; e += alpha p; r -= alpha q; z = D^-1 r;
+// rz1[c] += <r, z>; rr1[c] += <r, r>.
+__global__ void inner_update(int64_t n, int k, const double *rz, const double *pq,
+                             const float *dinv, const float *p, const float *q, float *e,
+                             float *r, float *z, double *rz1, double *rr1) {
+    extern __shared__ double s[];
+    double *s1 = s, *s2 = s + k;
+    sh_zero(s, 2 * k);
+    ColAcc a1(s1, k), a2(s2, k);
+    const int64_t tot = n * k;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % k);
+        const int64_t u = i / k;
+        const double den = pq[c];
+        const float a = (den > 0.0 && rz[c] > 0.0) ? (float)(rz[c] / den) : 0.f;
+        e[i] += a * p[i];
+        const float rv = r[i] - a * q[i];
+        r[i] = rv;
+        const float zv = dinv[u] * rv;
+        z[i] = zv;
+        a1.add(c, (double)rv * (double)zv);
+        a2.add(c, (double)rv * (double)rv);
+    }
+    a1.flush();
+    a2.flush();
+    __syncthreads();
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        if (s1[c] != 0.0) atomicAdd(&rz1[c], s1[c]);
+        if (s2[c] != 0.0) atomicAdd(&rr1[c], s2[c]);
+    }
+}
+
+// p = z + beta p, beta_c = rz1[c] / rz0[c].
+__global__ void inner_dir(int64_t n, int k, const double *rz0, const double *rz1, const float *z,
+                          float *p) {
+    const int64_t tot = n * k;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % k);
+        const float bta = rz0[c] > 0.0 ? (float)(rz1[c] / rz0[c]) : 0.f;
+        p[i] = z[i] + bta * p[i];
+    }
+}
+
+// X += |R_c| e.
+__global__ void outer_add(int64_t n, int k, const double *rnrm2, const float *e, double *X) {
+    const int64_t tot = n * k;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % k);
+        X[i] += sqrt(rnrm2[c]) * (double)e[i];
+    }
+}
+
+template <class F>
+void dispatch(const DevGraph &g, F f) {
+    if (g.off64) {
+        if (g.weighted) f(std::true_type{}, std::true_type{});
+        else f(std::true_type{}, std::false_type{});
+    } else {
+        if (g.weighted) f(std::false_type{}, std::true_type{});
+        else f(std::false_type{}, std::false_type{});
+    }
+}
+
+unsigned grid_for(int64_t work) {
+    const int64_t cap = (int64_t)num_sms() * 8;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(cap, (work + TPB - 1) / TPB));
+}
+
+}  // namespace
+
+// X = L^+ B for node-major FP64 B, X ([n][k]).  Internal entry.
+rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, double tol,
+                           int *iters_out, cudaStream_t st) {
+    const DevGraph &g = G->g;
+    const int64_t n = g.n;
+    if (k <= 0) return set_error(RWC_ERR_INVALID, "k must be positive");
+    if (tol <= 0) tol = 1e-10;
+    const int64_t nk = n * k;
+    const int max_inner = (int)std::min<int64_t>(200000, std::max<int64_t>(1000, 4 * n));
+    const int max_outer = 30;
+    const double inner_tol = 1e-5;
+    // device buffers
+    Buf buf(st);
+    const size_t fbytes = (size_t)nk * sizeof(float);
+    const size_t sc_per_it = 3 * (size_t)k;                 // pq, rz, rr per iteration
+    const size_t sc_count = (size_t)(max_inner + 4) * sc_per_it + 8 * (size_t)k;
+    const size_t bytes = (size_t)nk * sizeof(double) + 5 * fbytes + sc_count * sizeof(double) + 1024;
+    RWC_CUDA_TRY(cudaMallocAsync(&buf.p, bytes, st));
+    char *q = (char *)buf.p;
+    double *R = (double *)q; q += (size_t)nk * sizeof(double);
+    float *r = (float *)q; q += fbytes;
+    float *e = (float *)q; q += fbytes;
+    float *z = (float *)q; q += fbytes;
+    float *p = (float *)q; q += fbytes;
+    float *Qv = (float *)q; q += fbytes;
+    q = (char *)(((uintptr_t)q + 255) & ~(uintptr_t)255);
+    double *outer_sc = (double *)q;       // [0,k) colsum, [k,2k) |R|^2, [2k,3k) |B|^2
+    double *it_sc = outer_sc + 8 * (size_t)k;
+    const size_t shk = (size_t)k * sizeof(double), shk2 = 2 * shk;
+    const unsigned gs = grid_for(nk), gw = grid_for(n * 32);
+
+    RWC_CUDA_TRY(cudaMemsetAsync(X, 0, (size_t)nk * sizeof(double), st));
+    std::vector<double> h(3 * (size_t)k), bn(k);
+    int total_iters = 0;
+    double prev_worst = INFINITY;
+    for (int outer = 0; outer <= max_outer; ++outer) {
+        RWC_CUDA_TRY(cudaMemsetAsync(outer_sc, 0, 3 * shk, st));
+        dispatch(g, [&](auto o64, auto wt) {
+            ::rwc::count_launches(1); resid64<decltype(o64)::value, decltype(wt)::value><<<gw, TPB, shk, st>>>(g, k, B, X, R, outer_sc);
+        });
+        ::rwc::count_launches(1); center64<<<gs, TPB, shk, st>>>(n, k, R, outer_sc, outer_sc + k);
+        RWC_CUDA_TRY(cudaGetLastError());
+        RWC_CUDA_TRY(cudaMemcpyAsync(h.data(), outer_sc, 2 * shk, cudaMemcpyDeviceToHost, st));
+        RWC_CUDA_TRY(cudaStreamSynchronize(st));
+        if (outer == 0)
+            for (int c = 0; c < k; ++c) bn[c] = std::sqrt(h[k + c]);
+        double worst = 0.0;
+        for (int c = 0; c < k; ++c) {
+            const double rel = bn[c] > 0 ? std::sqrt(h[k + c]) / bn[c] : 0.0;
+            worst = std::max(worst, rel);
+        }
+        if (!(worst == worst)) return set_error(RWC_ERR_NOT_CONVERGED, "solver produced NaN");
+        if (worst <= tol) break;
+        if (outer == max_outer || (outer >= 3 && worst > 0.5 * prev_worst))
+            return set_error(RWC_ERR_NOT_CONVERGED, "Laplacian solve stalled at relative residual %.3g (tol %.3g)", worst, tol);
+        prev_worst = worst;
+        // inner FP32 PCG on the normalised residual
+        RWC_CUDA_TRY(cudaMemsetAsync(it_sc, 0, sc_count * sizeof(double) - 8 * shk, st));
+        ::rwc::count_launches(1); inner_start<<<gs, TPB, shk, st>>>(n, k, R, outer_sc + k, g.dinv32, r, e, z, p, it_sc + 1 * k);
+        int it = 0;
+        const int check = 16;
+        bool inner_done = false;
+        double best = INFINITY;
+        int since_best = 0;
+        while (!inner_done && it < max_inner) {
+            for (int j = 0; j < check && it < max_inner; ++j, ++it) {
+                double *pq = it_sc + (size_t)it * sc_per_it;          // slot it: pq
+                double *rz0 = it_sc + (size_t)it * sc_per_it + k;     // rz of iterate it
+                double *rz1 = it_sc + (size_t)(it + 1) * sc_per_it + k;
+                double *rr1 = it_sc + (size_t)(it + 1) * sc_per_it + 2 * k;
+                dispatch(g, [&](auto o64, auto wt) {
+                    ::rwc::count_launches(1); spmm32<decltype(o64)::value, decltype(wt)::value><<<gw, TPB, shk, st>>>(g, k, p, Qv, pq);
+                });
+                ::rwc::count_launches(1); inner_update<<<gs, TPB, shk2, st>>>(n, k, rz0, pq, g.dinv32, p, Qv, e, r, z, rz1, rr1);
+                ::rwc::count_launches(1); inner_dir<<<gs, TPB, 0, st>>>(n, k, rz0, rz1, z, p);
+            }
+            RWC_CUDA_TRY(cudaGetLastError());
+            RWC_CUDA_TRY(cudaMemcpyAsync(h.data(), it_sc + (size_t)it * sc_per_it + 2 * k, shk,
+                                         cudaMemcpyDeviceToHost, st));
+            RWC_CUDA_TRY(cudaStreamSynchronize(st));
+            double w2 = 0.0;
+            for (int c = 0; c < k; ++c) w2 = std::max(w2, h[c]);
+            if (std::sqrt(w2) <= inner_tol || !(w2 == w2)) inner_done = true;
+            // FP32 stagnation: no new minimum for 8 checks
+            if (w2 < 0.98 * best) { best = w2; since_best = 0; }
+            else if (++since_best >= 8) inner_done = true;
+        }
+        total_iters += it;
+        ::rwc::count_launches(1); outer_add<<<gs, TPB, 0, st>>>(n, k, outer_sc + k, e, X);
+        RWC_CUDA_TRY(cudaGetLastError());
+    }
+    // final projection of X onto 1-perp
+    RWC_CUDA_TRY(cudaMemsetAsync(outer_sc, 0, 2 * shk, st));
+    ::rwc::count_launches(1); colsum64<<<gs, TPB, shk, st>>>(n, k, X, outer_sc);
+    ::rwc::count_launches(1); center64<<<gs, TPB, shk, st>>>(n, k, X, outer_sc, outer_sc + k);
+    RWC_CUDA_TRY(cudaGetLastError());
+    if (iters_out) *iters_out = total_iters;
+    return RWC_OK;
+}
+
+}  // namespace rwc

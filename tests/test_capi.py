@@ -1,0 +1,82 @@
+"""C ABI: the library builds, loads and exports every symbol include/rwc.h
+declares; host-side validation rejects malformed graphs before touching the
+device (so these run without a GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2510_20604_gb300 as rwc
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "rwc.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:rwc_status|const char \*|int64_t)\s*(rwc_\w+)\s*\(", txt, re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2510_20604_gb300 import _build
+    _build.build()
+    L = ctypes.CDLL(rwc.lib_path)
+    syms = declared_symbols()
+    assert len(syms) >= 15
+    for s in syms:
+        assert hasattr(L, s), s
+    assert "sm_103a" in rwc.rwc_version()
+
+
+def test_binding_names_match_header():
+    for s in declared_symbols():
+        assert hasattr(rwc, s), s
+
+
+def _create(rp, col, w=None, root=-1, flags=0):
+    return rwc.rwc_graph_create(len(rp) - 1, rp[-1], np.array(rp, np.int64),
+                                np.array(col, np.int32), w, root, flags)
+
+
+@pytest.mark.parametrize("rp,col,w,why", [
+    ([0, 1], [0], None, "n must be >= 2"),
+    ([0, 2, 3], [0, 1, 0], None, "self-loop"),
+    ([0, 1, 1], [1], None, "isolated|reverse"),
+    ([0, 2, 3, 4], [2, 1, 0, 0], None, "sorted"),
+    ([0, 2, 1, 2], [1, 2], None, "decreases"),
+    ([0, 1, 2, 2], [1, 0], None, "isolated|reverse"),
+    ([0, 1, 2], [1, 0], np.array([1.0, 2.0], np.float32), "different weights"),
+    ([0, 1, 2], [1, 0], np.array([-1.0, -1.0], np.float32), "positive"),
+    ([0, 1, 2], [1, 0], np.array([np.nan, np.nan], np.float32), "positive"),
+    ([0, 2, 3, 4], [1, 2, 0, 1], None, "reverse"),
+    ([0, 1, 2], [5, 0], None, "out of range"),
+])
+def test_validation_rejects(rp, col, w, why):
+    with pytest.raises(rwc.RWCError) as e:
+        _create(rp, col, w)
+    assert e.value.status == 1
+    assert re.search(why, str(e.value)), str(e.value)
+
+
+def test_disconnected_graph_rejected():
+    a = synth.from_edges(4, [0, 2], [1, 3])   # two components
+    with pytest.raises(rwc.RWCError) as e:
+        _create(a.row_ptr, a.col)
+    assert e.value.status == 2
+
+
+def test_bad_root_rejected():
+    g = synth.path(5)
+    with pytest.raises(rwc.RWCError) as e:
+        _create(g.row_ptr, g.col, root=7)
+    assert e.value.status == 1
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    from paper_2510_20604_gb300 import _binding
+    monkeypatch.setattr(_binding, "_lib", None)
+    monkeypatch.setattr(_binding, "lib_path", "/nonexistent/librwc.so")
+    with pytest.raises(rwc.RWCError):
+        _binding.lib()

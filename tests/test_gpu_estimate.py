@@ -1,0 +1,82 @@
+"""GPU parity of the pivot solve and recovery (Algorithm 1) against the
+oracle: y against the dense NL^+[:, v]; H against the oracle's recovery on
+the same sums and the same y to 1e-12 relative; the solver against dense
+L^+; Monte Carlo error of the whole pipeline against exact FP64 H."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2510_20604_gb300 as rwc
+import synth
+from oracle import apprwc, exact
+from oracle import wilson as ow
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("gname", ["ba", "weighted", "grid"])
+def test_pivot_column_and_recovery(gname):
+    g = {"ba": lambda: synth.ba(500, 3, seed=1),
+         "weighted": lambda: synth.rgg(600, 10.0, seed=2, sigma=0.5),
+         "grid": lambda: synth.grid2d(20, 23)}[gname]()
+    G = rwc.Graph.from_synth(g)
+    T = 200
+    sums, _, _, _ = G.sample(T, seed=3)
+    H, y = G.estimate(sums, T, tol=1e-12, want_y=True)
+    yh = y.cpu().numpy()
+    yref = exact.pivot_column(g, G.root)
+    assert np.max(np.abs(yh - yref)) <= 1e-9 * np.max(np.abs(yref))
+    d = ow.wdeg(g)
+    Href = apprwc.recover_vec(d, G.root, sums.cpu().numpy() / T, yh)
+    rel = np.abs(H.cpu().numpy() - Href) / np.abs(Href)
+    assert rel.max() < 1e-12, rel.max()
+    # the recovery-only entry point gives the same numbers
+    H2 = torch.empty_like(H)
+    rwc.rwc_recover(G.handle, sums, T, y, H2)
+    assert torch.allclose(H, H2, rtol=1e-15, atol=0)
+
+
+def test_solver_against_dense_pseudoinverse():
+    g = synth.rgg(400, 9.0, seed=5, sigma=0.7)
+    G = rwc.Graph.from_synth(g)
+    L, _ = exact.laplacian(g)
+    P = exact.pinv_closed_form(L)
+    rng = np.random.default_rng(0)
+    k = 5
+    Bm = rng.standard_normal((k, g.n))
+    Bt = torch.tensor(Bm, dtype=torch.float64, device="cuda")
+    X = torch.empty_like(Bt)
+    it = rwc.rwc_solve(G.handle, k, Bt, X, 1e-11)
+    ref = (P @ Bm.T).T
+    err = np.abs(X.cpu().numpy() - ref).max() / np.abs(ref).max()
+    assert err < 1e-9, (err, it)
+
+
+def test_small_config_mre_against_exact():
+    """BA n=2000 + path, 1000 trees: MRE of the FastWalk estimate against the
+    dense FP64 ground truth, inside the band predicted by the geometric
+    variance of the visit counts (Lemma 5.2)."""
+    g = synth.ba(2000, 3, seed=0)
+    G = rwc.Graph.from_synth(g)
+    T = 1000
+    sums, _, _, _ = G.sample(T, seed=1)
+    H = G.estimate(sums, T).cpu().numpy()
+    Hx = exact.rwc_pinv(g)
+    mre = float(np.mean(np.abs(H - Hx) / Hx))
+    t = exact.tdiag(g, G.root)
+    d = ow.wdeg(g)
+    pi = d / d.sum()
+    pred = float(np.sqrt(2 / np.pi) * np.mean(np.sqrt(np.maximum(t * (t - 1), 0) / T) / pi / Hx))
+    assert 0.7 * pred < mre < 1.3 * pred, (mre, pred)
+    assert mre < 0.02
+
+
+def test_estimate_rejects_bad_arguments():
+    g = synth.path(10)
+    G = rwc.Graph.from_synth(g)
+    s = torch.zeros(10, dtype=torch.float64, device="cuda")
+    H = torch.empty_like(s)
+    with pytest.raises(rwc.RWCError):
+        rwc.rwc_estimate(G.handle, s, 0, 1e-10, H)
+    with pytest.raises(TypeError):
+        rwc.rwc_estimate(G.handle, s.float(), 1, 1e-10, H)

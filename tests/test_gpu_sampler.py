@@ -1,0 +1,147 @@
+"""GPU parity of the tree sampler against the oracle's sequential Wilson
+(Algorithm 3): parents and visit counts must be bit-identical for every tree,
+in both sampler modes, on special graphs, generated graphs spanning several
+tiles and chunks with ragged tails, weighted graphs (alias tables) and int64
+arc offsets; plus sampled trees at the benchmark's full sizes."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2510_20604_gb300 as rwc
+import synth
+from oracle import wilson as ow
+
+pytestmark = pytest.mark.gpu
+
+
+def run_both(g, T, seed=1, root=-1, tree0=0, opt=None, flags=0):
+    G = rwc.Graph.from_synth(g, root=root, flags=flags)
+    sums, st, par, vis = G.sample(T, seed=seed, tree0=tree0, want_trees=True, opt=opt)
+    ref = ow.Sampler(g, root=G.root, seed=seed).sample(tree0, T, want_trees=True)
+    return G, sums.cpu().numpy(), par.cpu().numpy(), vis.cpu().numpy(), ref, st
+
+
+def assert_exact(g, T, opt, seed=1, root=-1, tree0=0, flags=0):
+    G, sums, par, vis, ref, st = run_both(g, T, seed, root, tree0, opt, flags)
+    bad = np.nonzero((par != ref["parents"]).any(1) | (vis != ref["visits"]).any(1))[0]
+    assert len(bad) == 0, f"{len(bad)} trees differ, first {bad[:5]}"
+    assert np.array_equal(sums, ref["sums"])
+    return st
+
+
+SPECIAL = {
+    "edge": lambda: synth.path(2),
+    "star": lambda: synth.star(40, center=3),
+    "path": lambda: synth.path(60),
+    "cycle": lambda: synth.cycle(33),
+    "K7": lambda: synth.complete(7),
+    "grid2x2": lambda: synth.grid2d(2, 2),
+    "grid8x8": lambda: synth.grid2d(8, 8),
+    "grid5x7": lambda: synth.grid2d(5, 7),
+    "weighted": lambda: synth.rgg(80, 6.0, seed=4, sigma=1.0),
+}
+MODES = {"shared": rwc.Options(mode=rwc.MODE_SHARED),
+         "global": rwc.Options(mode=rwc.MODE_GLOBAL),
+         "global_nojump": rwc.Options(mode=rwc.MODE_GLOBAL, use_jumps=0),
+         "global_chunk3": rwc.Options(mode=rwc.MODE_GLOBAL, trees_per_chunk=3)}
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+@pytest.mark.parametrize("gname", list(SPECIAL))
+def test_special_graphs_bit_exact(gname, mode):
+    assert_exact(SPECIAL[gname](), 37, MODES[mode])
+
+
+@pytest.mark.parametrize("mode", ["shared", "global", "global_chunk3"])
+def test_small_ba_config_bit_exact(mode):
+    """BA n=2000, 3 edges per node + Hamiltonian path, unit weights, 1000
+    trees, Philox seed 1: every tree identical to the oracle's."""
+    g = synth.ba(2000, 3, seed=0)
+    opt = MODES[mode] if mode != "global_chunk3" else rwc.Options(mode=rwc.MODE_GLOBAL, trees_per_chunk=333)
+    assert_exact(g, 1000, opt)
+
+
+@pytest.mark.parametrize("mode", ["global", "global_nojump"])
+def test_grid_several_chunks_bit_exact(mode):
+    g = synth.grid2d(61, 67)
+    opt = rwc.Options(mode=rwc.MODE_GLOBAL, trees_per_chunk=9,
+                      use_jumps=0 if mode == "global_nojump" else -1)
+    assert_exact(g, 23, opt, root=-1)
+
+
+def test_weighted_rmat_int64_offsets_bit_exact():
+    g = synth.rmat(12, 16, seed=3, sigma=1.0)
+    assert_exact(g, 16, rwc.Options(mode=rwc.MODE_GLOBAL), flags=rwc.GRAPH_INT64_OFFSETS)
+    assert_exact(g, 8, rwc.Options(mode=rwc.MODE_GLOBAL))
+
+
+def test_weighted_rgg_shared_bit_exact():
+    g = synth.rgg(3000, 12.0, seed=1, sigma=0.5)
+    assert_exact(g, 40, rwc.Options(mode=rwc.MODE_SHARED))
+
+
+def test_tree_offset_and_shards_add_up():
+    g = synth.ba(1500, 3, seed=2)
+    G = rwc.Graph.from_synth(g)
+    a, _, _, _ = G.sample(50, seed=9)
+    b, _, _, _ = G.sample(20, seed=9)
+    G.sample(30, seed=9, tree0=20, sums=b)
+    assert torch.equal(a, b)
+    assert_exact(g, 10, rwc.Options(mode=rwc.MODE_GLOBAL), seed=9, tree0=4000000000)
+
+
+def test_seed_high_bits_matter():
+    g = synth.ba(300, 3, seed=2)
+    assert_exact(g, 5, rwc.Options(mode=rwc.MODE_SHARED), seed=(7 << 32) | 5)
+
+
+def test_explicit_root_and_empty_call():
+    g = synth.grid2d(10, 10)
+    assert_exact(g, 12, rwc.Options(mode=rwc.MODE_SHARED), root=55)
+    G = rwc.Graph.from_synth(g)
+    s = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+    st = rwc.rwc_sample_trees(G.handle, 1, 0, 0, s)
+    assert st.trees == 0 and float(s.abs().sum()) == 0.0
+
+
+def test_max_rounds_reports_not_converged():
+    g = synth.grid2d(30, 30)
+    G = rwc.Graph.from_synth(g)
+    for mode in (rwc.MODE_SHARED, rwc.MODE_GLOBAL):
+        with pytest.raises(rwc.RWCError) as e:
+            G.sample(4, opt=rwc.Options(mode=mode, max_rounds=2))
+        assert e.value.status == 4
+        # the handle stays usable afterwards
+        assert_exact(g, 3, rwc.Options(mode=mode))
+
+
+def _check_tree(g, root, par):
+    rp, col = g.row_ptr, g.col
+    n = g.n
+    assert par[root] == -1
+    src = np.arange(n)
+    m = src != root
+    # every parent arc exists
+    for u in np.nonzero(m)[0][:: max(1, n // 20000)]:
+        assert par[u] in col[rp[u]:rp[u + 1]]
+    # acyclic, reaches root: pointer jumping
+    p = par.copy()
+    p[root] = root
+    for _ in range(64):
+        p = p[p]
+    assert (p == root).all()
+
+
+@pytest.mark.parametrize("which", ["grid1024", "rmat20"])
+def test_full_size_sampled_trees(which):
+    """Benchmark graphs at full size, in the benchmark's launch configuration
+    (GLOBAL mode, auto chunk): a few trees, each compared with the oracle."""
+    g = synth.grid2d(1024, 1024) if which == "grid1024" else synth.rmat(20, 16, seed=0)
+    G = rwc.Graph.from_synth(g)
+    T = 2 if which == "grid1024" else 4
+    tree0 = 1000
+    sums, st, par, vis = G.sample(T, seed=1, tree0=tree0, want_trees=True)
+    ref = ow.Sampler(g, root=G.root, seed=1).sample(tree0, T, want_trees=True, nthreads=T)
+    assert np.array_equal(par.cpu().numpy(), ref["parents"])
+    assert np.array_equal(vis.cpu().numpy(), ref["visits"])
+    _check_tree(g, G.root, par[0].cpu().numpy())
