@@ -71,22 +71,25 @@ typedef struct {
 #define RWC_MODE_AUTO 0
 #define RWC_MODE_GLOBAL 1   /* rounds over tree chunks, state in HBM */
 #define RWC_MODE_SHARED 2   /* one thread block per tree, state in shared memory */
+#define RWC_MODE_WALKER 3   /* concurrent Wilson walkers, one block per tree, state in HBM */
 
 typedef struct {
-    int32_t mode;             /* RWC_MODE_*; AUTO picks SHARED when the tree fits */
+    int32_t mode;             /* RWC_MODE_*; AUTO picks SHARED when the tree fits in
+                                 shared memory, WALKER otherwise */
     int32_t max_rounds;       /* cap on popping rounds per chunk (0 = 1<<22) */
-    int64_t trees_per_chunk;  /* GLOBAL mode: trees resident at once (0 = auto) */
+    int64_t trees_per_chunk;  /* GLOBAL/WALKER: trees resident at once (0 = auto) */
     int32_t use_jumps;        /* GLOBAL mode: 1 = jump pointers (default), 0 = off,
                                  -1 = default */
-    int32_t block_threads;    /* SHARED mode block size (0 = auto) */
-    int64_t memory_budget;    /* GLOBAL mode: bytes of scratch to use (0 = auto) */
+    int32_t block_threads;    /* SHARED: block size; WALKER: walkers per tree (0 = auto) */
+    int64_t memory_budget;    /* GLOBAL/WALKER: bytes of scratch to use (0 = auto) */
     int32_t profile;          /* 1 = time every kernel launch with CUDA events on
                                  the call's stream (fills rwc_stats_t.phase_*) */
     int32_t reserved;
 } rwc_options_t;
 
-/* Sampler phases reported in rwc_stats_t (GLOBAL mode; SHARED mode reports
- * its single kernel as RWC_PHASE_WALK). */
+/* Sampler phases reported in rwc_stats_t.  GLOBAL mode: INIT, WALK, POP
+ * (classification is part of POP), ACCUM.  WALKER mode: INIT, WALK (the walker
+ * kernel), ACCUM.  SHARED mode reports its single kernel as WALK. */
 #define RWC_PHASE_INIT 0      /* first successor of every vertex */
 #define RWC_PHASE_WALK 1      /* marked vertex -> next marked or settled vertex */
 #define RWC_PHASE_CLASSIFY 2  /* cycle leaders on the compressed graph */
@@ -98,8 +101,8 @@ typedef struct {
 typedef struct {
     int64_t trees;        /* trees sampled by the last call */
     int64_t draws;        /* successor draws (= sum of visits over all trees) */
-    int64_t rounds;       /* popping rounds, summed over chunks */
-    int64_t walk_steps;   /* pointer-chasing steps of the cycle detection */
+    int64_t rounds;       /* GLOBAL/SHARED: popping rounds; WALKER: yielded walks */
+    int64_t walk_steps;   /* GLOBAL: pointer-chasing steps; WALKER: walker steps */
     int64_t chunks;       /* tree chunks processed */
     int32_t mode;         /* mode actually used */
     int32_t reserved;

@@ -17,7 +17,8 @@ the same expression with sum_v c_v (phi_e)_v^2 replaced by
 ||Q C^1/2 L^+ b_e||^2 and sum_v c_v L^+_vv by the Hutchinson estimate
 tr(Q C^1/2 L^+ C^1/2 Q^T), for a given k x n matrix Q (Johnson-Lindenstrauss
 sketch; Q = I gives the exact value).  ``grad_fd`` is the central finite
-difference of the dense J.
+difference of the dense J.  ``grad_sketch_sparse`` is ``grad_sketch`` for
+large graphs at selected edges, with SciPy's sparse CG as the solve.
 
 Pins (tests/test_oracle_grad.py): closed form against the finite difference;
 the sketch with Q = I against the closed form; the sketch's mean over many
@@ -94,3 +95,41 @@ def grad_fd(n, a, b, w, c, h=1e-5) -> np.ndarray:
         wm = w.copy(); wm[e] -= h
         g[e] = (J(n, a, b, wp, c) - J(n, a, b, wm, c)) / (2.0 * h)
     return g
+
+
+def grad_sketch_sparse(n, a, b, w, c, Q, edges, tol=1e-12):
+    """``grad_sketch`` for large graphs at selected edges only: the same
+    expression with L^+ applied by a sparse conjugate-gradient solve (SciPy,
+    one solve per column of [C^1/2 Q^T, c, d], each right-hand side projected
+    onto 1-perp first)."""
+    import scipy.sparse as sp
+    from scipy.sparse.linalg import cg
+    w = np.asarray(w, np.float64)
+    c = np.asarray(c, np.float64)
+    A = sp.coo_matrix((np.concatenate([w, w]), (np.concatenate([a, b]), np.concatenate([b, a]))),
+                      shape=(n, n)).tocsr()
+    d = np.asarray(A.sum(axis=1)).ravel()
+    L = (sp.diags(d) - A).tocsr()
+    Minv = sp.diags(1.0 / d)
+
+    def pinv_apply(v):
+        v = v - v.mean()
+        try:
+            x, info = cg(L, v, rtol=tol, atol=0.0, maxiter=20 * n, M=Minv)
+        except TypeError:  # SciPy < 1.12 names the relative tolerance `tol`
+            x, info = cg(L, v, tol=tol, atol=0.0, maxiter=20 * n, M=Minv)
+        if info != 0:
+            raise RuntimeError("oracle CG did not converge")
+        return x - x.mean()
+
+    k = Q.shape[0]
+    sc = np.sqrt(c)
+    Z = np.stack([pinv_apply(sc * Q[i]) for i in range(k)])   # Q C^1/2 L^+
+    x = pinv_apply(c)
+    y = pinv_apply(d)
+    vol = d.sum()
+    trCP = float(np.sum(Z * (Q * sc[None, :])))
+    ea, eb = a[edges], b[edges]
+    diff = Z[:, ea] - Z[:, eb]
+    sq = (diff * diff).sum(axis=0)
+    return _assemble(ea, eb, trCP, sq, x, y, d, vol, c.sum())

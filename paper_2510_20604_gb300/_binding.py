@@ -9,7 +9,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 lib_path = os.path.join(HERE, "librwc.so")
 
-MODE_AUTO, MODE_GLOBAL, MODE_SHARED = 0, 1, 2
+MODE_AUTO, MODE_GLOBAL, MODE_SHARED, MODE_WALKER = 0, 1, 2, 3
 NPHASE = 6
 PHASES = ("init", "walk", "classify", "pop", "finish", "accum")
 GRAPH_INT64_OFFSETS, GRAPH_SKIP_CONNECTIVITY = 0x1, 0x2

@@ -154,6 +154,7 @@ def _make_function():
             g = Graph(row_ptr, col_idx, warc)
             H, _ = fastwalk(g, num_trees, seed)
             ctx.g, ctx.k, ctx.sketch_seed = g, k, sketch_seed
+            ctx.w_device = w.device
             return H.to(w.dtype)
 
         @staticmethod
@@ -163,7 +164,7 @@ def _make_function():
             grad = ctx.g.grad(pos.contiguous(), ctx.k, ctx.sketch_seed).double()
             if bool((neg > 0).any()):
                 grad = grad - ctx.g.grad(neg.contiguous(), ctx.k, ctx.sketch_seed).double()
-            return grad.to(gout.dtype), None, None, None, None, None, None
+            return grad.to(device=ctx.w_device, dtype=gout.dtype), None, None, None, None, None, None
 
     return RWCFunction
 

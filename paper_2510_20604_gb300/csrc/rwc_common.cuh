@@ -66,11 +66,18 @@ struct rwc_graph {
     int nallocs = 0;
     // pinned host scalars used by synchronising entry points
     int64_t *host_scalars = nullptr;
+    // start order of the walker sampler (device, n-1 entries), made on first use
+    int32_t *walk_order = nullptr;
 };
 
 namespace rwc {
 
 cudaError_t graph_alloc(rwc_graph *G, void **p, size_t bytes);
+
+// Walker sampler (walker.cu).
+rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, double *sums,
+                         int32_t *parents, int32_t *visits, const rwc_options_t &o,
+                         rwc_stats_t *st, cudaStream_t stream);
 
 // Host-side CSR checks (graph.cu): see rwc_graph_create for the rules.
 rwc_status validate_csr(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *col,

@@ -40,14 +40,19 @@ namespace {
 
 constexpr int32_t TAG_FREE = -1;
 constexpr int32_t TAG_SETTLED = -2;
-constexpr int8_t CLS_OTHER = 0, CLS_LEADER = 1, CLS_TREE = 2;
+constexpr int8_t CLS_OTHER = 0, CLS_LEADER = 1, CLS_TREE = 2;  // compressed-node classes
 
 constexpr int ERR_BRENT = 1;     // compressed walk exceeded its bound
 constexpr int ERR_LOOP = 4;      // a pointer chase exceeded n steps (internal error)
 
 // ------------------------------------------------------------- GLOBAL mode
-// Per (tree, vertex) record, 32 bytes: w0 = p | tag << 32, w1 = k,
-// w2 = J | kj << 32 (jump target and the target's pop count), w3 unused.
+// Per (tree, vertex) record, 32 bytes:
+//   w0 = p | tag << 32   (successor; tag = SETTLED, or the index in the marked
+//                         list of round `stamp`)
+//   w1 = k | stamp << 32 (pop count; round in which the vertex was last marked)
+//   w2 = J | kj << 32    (jump target and the target's pop count when recorded)
+// A vertex is marked in round r iff tag >= 0 and stamp == r, so marks of
+// earlier rounds need no reset.
 struct __align__(32) VRec {
     unsigned long long w0, w1, w2, w3;
 };
@@ -59,16 +64,26 @@ __device__ __forceinline__ unsigned long long pack(int32_t lo, int32_t hi) {
 }
 __device__ __forceinline__ int32_t *tag_ptr(VRec *r) { return reinterpret_cast<int32_t *>(&r->w0) + 1; }
 
+// first two words of a record in one 16-byte load
+__device__ __forceinline__ ulonglong2 head(const VRec *r) {
+    return *reinterpret_cast<const ulonglong2 *>(r);
+}
+// settled, or marked in round rr
+__device__ __forceinline__ bool stops(ulonglong2 h, int32_t rr) {
+    const int32_t tag = hi32(h.x);
+    return tag == TAG_SETTLED || (tag >= 0 && hi32(h.y) == rr);
+}
+
 struct GState {
     VRec *rec;                 // [B][n]
-    unsigned long long *M[2];  // marked lists: (tree << 32) | u
-    int64_t *cnt;              // [2] list lengths
+    unsigned long long *M[2];  // marked lists: (tree << 32) | u; round r uses M[r & 1]
     int32_t *nm;               // [cap] compressed successor (-1 = reaches root)
-    int8_t *cls;               // [cap]
-    uint8_t *popped;           // [cap]
+    int64_t *cnt;              // [2] list lengths
     int *err;                  // device error word
+    unsigned *done;            // blocks finished in the current pop launch
     unsigned long long *steps; // walk-step counter
     unsigned long long *marked;// marked entries over all rounds (= draws)
+    int *round;                // current round (starts at 1)
     int64_t cap;
 };
 
@@ -84,25 +99,30 @@ __global__ void __launch_bounds__(256) g_init(DevGraph g, GState s, int64_t B, u
         VRec r;
         if (u == root) {
             r.w0 = pack(-1, TAG_SETTLED);
+            r.w1 = 0ull;
         } else {
             const int64_t ord = t * (n - 1) + (u < root ? u : u - 1);
             const int32_t p = succ<OFF64, W>(g, u, 0u, tree0 + (uint32_t)t, 0u, k0, k1);
             r.w0 = pack(p, (int32_t)ord);
-            s.M[0][ord] = ((unsigned long long)t << 32) | (uint32_t)u;
+            r.w1 = pack(0, 1);
+            s.M[1][ord] = ((unsigned long long)t << 32) | (uint32_t)u;
         }
-        r.w1 = 0ull;
         r.w2 = pack(-1, 0);
         r.w3 = 0ull;
         s.rec[idx] = r;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        s.cnt[0] = B * (n - 1);
-        s.cnt[1] = 0;
+        s.cnt[0] = 0;
+        s.cnt[1] = B * (n - 1);
+        *s.round = 1;
+        *s.done = 0;
     }
 }
 
 // Phase 1: walk from every marked vertex to the next marked or settled vertex.
-__global__ void __launch_bounds__(256) g_walk(const int64_t n, GState s, int cur, int use_jumps) {
+__global__ void __launch_bounds__(256) g_walk(const int64_t n, GState s, int use_jumps) {
+    const int32_t rr = *s.round;
+    const int cur = rr & 1;
     const int64_t m = s.cnt[cur];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         s.cnt[cur ^ 1] = 0;
@@ -118,42 +138,43 @@ __global__ void __launch_bounds__(256) g_walk(const int64_t n, GState s, int cur
         int32_t x = first, last = -1;
         uint32_t klast = 0;
         int64_t plain = 0, steps = 0;
-        int32_t tagx;
+        ulonglong2 hx;
         for (;;) {
-            const unsigned long long w0 = base[x].w0;
-            tagx = hi32(w0);
-            if (tagx != TAG_FREE) break;
-            if (++steps > n) { atomicOr(s.err, ERR_LOOP); tagx = TAG_SETTLED; break; }
+            hx = head(base + x);
+            if (stops(hx, rr)) break;
+            if (++steps > n) { atomicOr(s.err, ERR_LOOP); hx.x = pack(0, TAG_SETTLED); break; }
             if (use_jumps) {
                 const unsigned long long w2 = base[x].w2;
                 const int32_t J = lo32(w2);
                 if (J >= 0) {
-                    const unsigned long long j0 = base[J].w0, j1 = base[J].w1;
-                    if ((uint32_t)j1 == (uint32_t)(w2 >> 32)) {
-                        last = J; klast = (uint32_t)j1;
-                        x = lo32(j0);
+                    const ulonglong2 hj = head(base + J);
+                    if ((uint32_t)hj.y == (uint32_t)(w2 >> 32)) {
+                        last = J; klast = (uint32_t)hj.y;
+                        x = lo32(hj.x);
                         continue;
                     }
                 }
             }
             last = x;
-            klast = (uint32_t)base[x].w1;
-            x = lo32(w0);
+            klast = (uint32_t)hx.y;
+            x = lo32(hx.x);
             ++plain;
         }
         local_steps += steps + 1;
-        if (tagx == TAG_SETTLED) {
+        if (hi32(hx.x) == TAG_SETTLED) {
             // the whole segment reaches the root: settle what we can see
             s.nm[i] = -1;
             *tag_ptr(base + u) = TAG_SETTLED;
             int32_t y = first;
-            for (int64_t q = 0; hi32(base[y].w0) == TAG_FREE; ++q) {
+            for (int64_t q = 0;; ++q) {
+                const ulonglong2 hy = head(base + y);
+                if (stops(hy, rr)) break;
                 if (q > n) { atomicOr(s.err, ERR_LOOP); break; }
                 *tag_ptr(base + y) = TAG_SETTLED;
-                y = lo32(base[y].w0);
+                y = lo32(hy.x);
             }
         } else {
-            s.nm[i] = tagx;
+            s.nm[i] = hi32(hx.x);
             if (use_jumps && plain > 2 && last >= 0) {
                 // path compression: every vertex of the segment jumps to `last`
                 int32_t y = first;
@@ -173,28 +194,6 @@ __global__ void __launch_bounds__(256) g_walk(const int64_t n, GState s, int cur
     if (local_steps) atomicAdd(s.steps, local_steps);
 }
 
-// Phase 2: classify compressed nodes (leader of a cycle / reaches root / other).
-__global__ void __launch_bounds__(256) g_classify(GState s, int cur) {
-    const int64_t m = s.cnt[cur];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t x = s.nm[i];
-        int64_t saved = -3, power = 1, lam = 0;
-        int8_t c = CLS_OTHER;
-        for (int64_t it = 0;; ++it) {
-            if (x < 0) { c = CLS_TREE; break; }
-            if (x == i) { c = CLS_LEADER; break; }
-            if (x < i) { c = CLS_OTHER; break; }
-            if (x == saved) { c = CLS_OTHER; break; }
-            if (it > 2 * m + 4) { atomicOr(s.err, ERR_BRENT); break; }
-            if (++lam == power) { saved = x; power <<= 1; lam = 0; }
-            x = s.nm[x];
-        }
-        s.cls[i] = c;
-        s.popped[i] = 0;
-    }
-}
-
 __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t &total) {
     __shared__ int64_t warp_sums[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -207,13 +206,13 @@ __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t &total) {
     if (lane == 31) warp_sums[wid] = x;
     __syncthreads();
     if (wid == 0) {
-        int64_t s = lane < nw ? warp_sums[lane] : 0;
+        int64_t t = lane < nw ? warp_sums[lane] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int64_t y = __shfl_up_sync(0xffffffffu, s, o);
-            if (lane >= o) s += y;
+            const int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
         }
-        if (lane < nw) warp_sums[lane] = s;
+        if (lane < nw) warp_sums[lane] = t;
     }
     __syncthreads();
     const int64_t before = (wid > 0 ? warp_sums[wid - 1] : 0) + x - v;
@@ -222,11 +221,15 @@ __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t &total) {
     return before;
 }
 
-// Phase 3: leaders pop their cycles; nodes that reach the root settle.
+// Phase 2: classify each compressed node (leader of a cycle / reaches the
+// root / other) and let the leaders pop their cycles; the last block to
+// finish advances the round.
 template <bool OFF64, bool W>
-__global__ void __launch_bounds__(256) g_pop(DevGraph g, GState s, int cur, uint32_t tree0,
-                                             uint32_t k0, uint32_t k1) {
+__global__ void __launch_bounds__(256) g_pop(DevGraph g, GState s, uint32_t tree0, uint32_t k0,
+                                             uint32_t k1) {
     const int64_t n = g.n;
+    const int32_t rr = *s.round;
+    const int cur = rr & 1;
     const int64_t m = s.cnt[cur];
     __shared__ int64_t blockbase;
     for (int64_t chunk = blockIdx.x * (int64_t)blockDim.x; chunk < m;
@@ -238,11 +241,22 @@ __global__ void __launch_bounds__(256) g_pop(DevGraph g, GState s, int cur, uint
         int64_t t = 0;
         int8_t c = CLS_OTHER;
         if (i < m) {
+            // Brent's cycle detection on the compressed graph; the smallest
+            // index of a cycle is its leader
+            int64_t x = s.nm[i];
+            int64_t saved = -3, power = 1, lam = 0;
+            for (int64_t it = 0;; ++it) {
+                if (x < 0) { c = CLS_TREE; break; }
+                if (x == i) { c = CLS_LEADER; break; }
+                if (x < i || x == saved) break;
+                if (it > 2 * m + 4) { atomicOr(s.err, ERR_BRENT); break; }
+                if (++lam == power) { saved = x; power <<= 1; lam = 0; }
+                x = s.nm[x];
+            }
             const unsigned long long e = s.M[cur][i];
             t = (int64_t)(e >> 32);
             base = s.rec + t * n;
             u0 = (int32_t)(uint32_t)e;
-            c = s.cls[i];
             if (c == CLS_LEADER) {
                 int32_t w = u0;
                 do {
@@ -253,21 +267,20 @@ __global__ void __launch_bounds__(256) g_pop(DevGraph g, GState s, int cur, uint
         }
         int64_t total;
         const int64_t off = block_excl_scan(len, total);
-        if (threadIdx.x == 0) blockbase = total ? (int64_t)atomicAdd((unsigned long long *)&s.cnt[cur ^ 1], (unsigned long long)total) : 0;
+        if (threadIdx.x == 0)
+            blockbase = total ? (int64_t)atomicAdd((unsigned long long *)&s.cnt[cur ^ 1], (unsigned long long)total) : 0;
         __syncthreads();
         if (len) {
             int64_t pos = blockbase + off;
             int32_t w = u0;
             const uint32_t tree = tree0 + (uint32_t)t;
             do {
-                const unsigned long long w0 = base[w].w0;
-                const int32_t nx = lo32(w0);
-                const int32_t tg = hi32(w0);
-                if (tg >= 0) s.popped[tg] = 1;
-                const uint32_t k = (uint32_t)base[w].w1 + 1u;
+                const ulonglong2 hw = head(base + w);
+                const int32_t nx = lo32(hw.x);
+                const uint32_t k = (uint32_t)hw.y + 1u;
                 const int32_t p = succ<OFF64, W>(g, w, k, tree, 0u, k0, k1);
                 base[w].w0 = pack(p, (int32_t)pos);
-                base[w].w1 = (unsigned long long)k;
+                base[w].w1 = pack((int32_t)k, rr + 1);
                 base[w].w2 = pack(-1, 0);
                 s.M[cur ^ 1][pos] = ((unsigned long long)t << 32) | (uint32_t)w;
                 ++pos;
@@ -277,25 +290,21 @@ __global__ void __launch_bounds__(256) g_pop(DevGraph g, GState s, int cur, uint
         if (c == CLS_TREE) {
             int32_t y = u0;
             int64_t q = 0;
-            do {
+            for (;;) {
                 if (++q > n) { atomicOr(s.err, ERR_LOOP); break; }
                 *tag_ptr(base + y) = TAG_SETTLED;
                 y = lo32(base[y].w0);
-            } while (hi32(base[y].w0) == TAG_FREE);
+                if (stops(head(base + y), rr)) break;
+            }
         }
         __syncthreads();
     }
-}
-
-// Phase 4: marked vertices that were not popped return to the free pool.
-__global__ void __launch_bounds__(256) g_finish(const int64_t n, GState s, int cur) {
-    const int64_t m = s.cnt[cur];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        if (s.popped[i]) continue;
-        const unsigned long long e = s.M[cur][i];
-        VRec *r = s.rec + (int64_t)(e >> 32) * n + (int32_t)(uint32_t)e;
-        if (hi32(r->w0) == (int32_t)i) *tag_ptr(r) = TAG_FREE;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(s.done, 1u) == gridDim.x - 1) {
+            *s.done = 0;
+            *s.round = rr + 1;
+        }
     }
 }
 
@@ -404,7 +413,7 @@ static rwc_status sample_global(rwc_graph *G, uint64_t seed, int64_t tree0, int6
                                 rwc_stats_t *st, cudaStream_t stream) {
     const DevGraph &g = G->g;
     const int64_t n = g.n;
-    const size_t per_tree = (size_t)n * (sizeof(VRec) + 2 * 8 + 4 + 1 + 1) + 256;
+    const size_t per_tree = (size_t)n * (sizeof(VRec) + 2 * 8 + 4) + 256;
     int64_t B = o.trees_per_chunk;
     if (B <= 0) {
         size_t fr = 0, tot = 0;
@@ -413,15 +422,15 @@ static rwc_status sample_global(rwc_graph *G, uint64_t seed, int64_t tree0, int6
         B = (int64_t)std::max<size_t>(1, budget / per_tree);
     }
     B = std::min(B, T);
-    if (B > (int64_t)0x7fffffff / 2) B = 0x3fffffff;
+    // list indices are int32 tags
+    B = std::min<int64_t>(B, std::max<int64_t>(1, ((int64_t)1 << 31) / std::max<int64_t>(1, n - 1) - 1));
     const int use_jumps = o.use_jumps < 0 ? 1 : o.use_jumps;
     const int64_t max_rounds = o.max_rounds > 0 ? o.max_rounds : (1 << 22);
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     const int64_t cap = B * (n - 1);
 
     Scratch scr(stream);
-    const size_t bytes = (size_t)B * n * sizeof(VRec) + 2 * (size_t)cap * 8 + (size_t)cap * 4 +
-                         2 * (size_t)cap + 256;
+    const size_t bytes = (size_t)B * n * sizeof(VRec) + 2 * (size_t)cap * 8 + (size_t)cap * 4 + 256;
     RWC_CUDA_TRY(cudaMallocAsync(&scr.p, bytes, stream));
     char *p = (char *)scr.p;
     GState s;
@@ -429,105 +438,124 @@ static rwc_status sample_global(rwc_graph *G, uint64_t seed, int64_t tree0, int6
     s.M[0] = (unsigned long long *)p; p += (size_t)cap * 8;
     s.M[1] = (unsigned long long *)p; p += (size_t)cap * 8;
     s.nm = (int32_t *)p; p += (size_t)cap * 4;
-    s.cls = (int8_t *)p; p += (size_t)cap;
-    s.popped = (uint8_t *)p; p += (size_t)cap;
     p = (char *)(((uintptr_t)p + 63) & ~(uintptr_t)63);
-    s.cnt = (int64_t *)p;
-    s.err = (int *)(p + 16);
-    s.steps = (unsigned long long *)(p + 24);
-    s.marked = (unsigned long long *)(p + 32);
+    // scratch tail: cnt[2] @0, err @16, done @20, steps @24, marked @32, round @40
+    char *tail = p;
+    s.cnt = (int64_t *)tail;
+    s.err = (int *)(tail + 16);
+    s.done = (unsigned *)(tail + 20);
+    s.steps = (unsigned long long *)(tail + 24);
+    s.marked = (unsigned long long *)(tail + 32);
+    s.round = (int *)(tail + 40);
     s.cap = cap;
+
     const bool prof = o.profile != 0;
-    constexpr int MAXQ = 64, NPH = 4;
+    constexpr int Q = 32;          // rounds per captured graph
+    // events: [2q], [2q+1] around walk of round q; [2Q + 2q], +1 around pop;
+    // [4Q..4Q+3] around init and accum
     std::vector<cudaEvent_t> ev;
     if (prof) {
-        ev.resize(2 * (MAXQ * NPH + 2));
+        ev.resize(4 * Q + 4);
         for (auto &e : ev) cudaEventCreate(&e);
     }
-    struct EvGuard {
+    struct Guard {
         std::vector<cudaEvent_t> &v;
-        ~EvGuard() { for (auto e : v) cudaEventDestroy(e); }
-    } evguard{ev};
-    auto ev_ms = [&](int i) {
+        cudaGraphExec_t exec = nullptr;
+        cudaStream_t cs = nullptr;
+        ~Guard() {
+            for (auto e : v) cudaEventDestroy(e);
+            if (exec) cudaGraphExecDestroy(exec);
+            if (cs) cudaStreamDestroy(cs);
+        }
+    } guard{ev};
+    auto ms_between = [&](int a, int b) {
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+        cudaEventElapsedTime(&ms, ev[a], ev[b]);
         return (double)ms;
     };
-    int64_t tot_steps = 0, tot_marked = 0;
-
+    RWC_CUDA_TRY(cudaStreamCreateWithFlags(&guard.cs, cudaStreamNonBlocking));
     const int sms = num_sms();
     const unsigned grid = (unsigned)(sms * 8);
     int64_t *h = G->host_scalars;
+    int64_t tot_steps = 0, tot_marked = 0;
     for (int64_t c0 = 0; c0 < T; c0 += B) {
         const int64_t Bc = std::min(B, T - c0);
         const uint32_t t0 = (uint32_t)(tree0 + c0);
-        RWC_CUDA_TRY(cudaMemsetAsync(s.cnt, 0, 48, stream));
-        const int IEV = MAXQ * NPH;   // event slots for init / accum
-        if (prof) cudaEventRecord(ev[2 * IEV], stream);
+        RWC_CUDA_TRY(cudaMemsetAsync(tail, 0, 48, stream));
+        if (prof) cudaEventRecord(ev[4 * Q], stream);
         dispatch(g, [&](auto off64, auto wt) {
             constexpr bool O = decltype(off64)::value, Wt = decltype(wt)::value;
-            ::rwc::count_launches(1); g_init<O, Wt><<<grid, 256, 0, stream>>>(g, s, Bc, t0, k0, k1);
+            ::rwc::count_launches(1);
+            g_init<O, Wt><<<grid, 256, 0, stream>>>(g, s, Bc, t0, k0, k1);
         });
-        if (prof) cudaEventRecord(ev[2 * IEV + 1], stream);
+        if (prof) cudaEventRecord(ev[4 * Q + 1], stream);
         RWC_CUDA_TRY(cudaGetLastError());
-        int64_t r = 0;
-        int check_every = 4;
-        bool done = false;
-        while (!done) {
-            for (int q = 0; q < check_every; ++q, ++r) {
-                const int cur = (int)(r & 1);
-                auto rec = [&](int ph, int end) {
-                    if (prof) cudaEventRecord(ev[2 * (q * NPH + ph) + end], stream);
-                };
-                rec(0, 0);
-                ::rwc::count_launches(1); g_walk<<<grid, 256, 0, stream>>>(n, s, cur, use_jumps);
-                rec(0, 1); rec(1, 0);
-                ::rwc::count_launches(1); g_classify<<<grid, 256, 0, stream>>>(s, cur);
-                rec(1, 1); rec(2, 0);
+        // capture Q rounds once per chunk; replays advance the device round
+        if (guard.exec) { cudaGraphExecDestroy(guard.exec); guard.exec = nullptr; }
+        {
+            cudaGraph_t gr = nullptr;
+            RWC_CUDA_TRY(cudaStreamBeginCapture(guard.cs, cudaStreamCaptureModeThreadLocal));
+            for (int q = 0; q < Q; ++q) {
+                if (prof) cudaEventRecord(ev[2 * q], guard.cs);
+                g_walk<<<grid, 256, 0, guard.cs>>>(n, s, use_jumps);
+                if (prof) { cudaEventRecord(ev[2 * q + 1], guard.cs); cudaEventRecord(ev[2 * Q + 2 * q], guard.cs); }
                 dispatch(g, [&](auto off64, auto wt) {
                     constexpr bool O = decltype(off64)::value, Wt = decltype(wt)::value;
-                    ::rwc::count_launches(1); g_pop<O, Wt><<<grid, 256, 0, stream>>>(g, s, cur, t0, k0, k1);
+                    g_pop<O, Wt><<<grid, 256, 0, guard.cs>>>(g, s, t0, k0, k1);
                 });
-                rec(2, 1); rec(3, 0);
-                ::rwc::count_launches(1); g_finish<<<grid, 256, 0, stream>>>(n, s, cur);
-                rec(3, 1);
+                if (prof) cudaEventRecord(ev[2 * Q + 2 * q + 1], guard.cs);
             }
-            RWC_CUDA_TRY(cudaGetLastError());
-            RWC_CUDA_TRY(cudaMemcpyAsync(h, s.cnt, 40, cudaMemcpyDeviceToHost, stream));
+            const cudaError_t ce = cudaStreamEndCapture(guard.cs, &gr);
+            if (ce != cudaSuccess) {
+                if (gr) cudaGraphDestroy(gr);
+                return set_error(RWC_ERR_CUDA, "capturing the round graph failed: %s", cudaGetErrorString(ce));
+            }
+            const cudaError_t ie = cudaGraphInstantiate(&guard.exec, gr, 0);
+            cudaGraphDestroy(gr);
+            RWC_CUDA_TRY(ie);
+        }
+        int64_t rounds = 0;
+        for (;;) {
+            ::rwc::count_launches(2 * Q);
+            RWC_CUDA_TRY(cudaGraphLaunch(guard.exec, stream));
+            rounds += Q;
+            RWC_CUDA_TRY(cudaMemcpyAsync(h, tail, 48, cudaMemcpyDeviceToHost, stream));
             RWC_CUDA_TRY(cudaStreamSynchronize(stream));
             if (prof && st) {
-                static const int phase_of[NPH] = {RWC_PHASE_WALK, RWC_PHASE_CLASSIFY, RWC_PHASE_POP,
-                                                  RWC_PHASE_FINISH};
-                for (int q = 0; q < check_every; ++q)
-                    for (int ph = 0; ph < NPH; ++ph) {
-                        st->phase_ms[phase_of[ph]] += ev_ms(q * NPH + ph);
-                        st->phase_launches[phase_of[ph]] += 1;
-                    }
+                for (int q = 0; q < Q; ++q) {
+                    st->phase_ms[RWC_PHASE_WALK] += ms_between(2 * q, 2 * q + 1);
+                    st->phase_ms[RWC_PHASE_POP] += ms_between(2 * Q + 2 * q, 2 * Q + 2 * q + 1);
+                }
+                st->phase_launches[RWC_PHASE_WALK] += Q;
+                st->phase_launches[RWC_PHASE_POP] += Q;
             }
-            if ((h[2] & 0xffffffff) != 0)
-                return set_error(RWC_ERR_CUDA, "sampler internal check failed (code %d)", (int)(h[2] & 0xffffffff));
-            if (h[r & 1] == 0) done = true;
-            else if (r >= max_rounds) return set_error(RWC_ERR_NOT_CONVERGED, "cycle popping exceeded max_rounds (%lld)", (long long)max_rounds);
-            check_every = std::min(check_every * 2, MAXQ);
+            const int err = (int)(h[2] & 0xffffffff);
+            if (err)
+                return set_error(RWC_ERR_CUDA, "sampler internal check failed (code %d)", err);
+            const int32_t rr = (int32_t)(h[5] & 0xffffffff);
+            if (h[rr & 1] == 0) break;
+            if (rounds >= max_rounds)
+                return set_error(RWC_ERR_NOT_CONVERGED, "cycle popping exceeded max_rounds (%lld)", (long long)max_rounds);
         }
-        if (prof) cudaEventRecord(ev[2 * (IEV + 1)], stream);
-        ::rwc::count_launches(1); g_accum<<<grid, 256, 0, stream>>>(n, g.root, s.rec, Bc, sums,
+        if (prof) cudaEventRecord(ev[4 * Q + 2], stream);
+        ::rwc::count_launches(1);
+        g_accum<<<grid, 256, 0, stream>>>(n, g.root, s.rec, Bc, sums,
                                           parents ? parents + c0 * n : nullptr,
                                           visits ? visits + c0 * n : nullptr);
-        if (prof) cudaEventRecord(ev[2 * (IEV + 1) + 1], stream);
+        if (prof) cudaEventRecord(ev[4 * Q + 3], stream);
         RWC_CUDA_TRY(cudaGetLastError());
         RWC_CUDA_TRY(cudaStreamSynchronize(stream));
         tot_steps += (int64_t)h[3];
         tot_marked += (int64_t)h[4];
         if (st) {
-            st->rounds += r;
+            st->rounds += (int64_t)(h[5] & 0xffffffff) - 1;
             st->chunks += 1;
             st->phase_units[RWC_PHASE_INIT] += Bc * n;
             st->phase_units[RWC_PHASE_ACCUM] += Bc * n;
             st->phase_units[RWC_PHASE_POP] += (int64_t)h[4] - Bc * (n - 1);
             if (prof) {
-                st->phase_ms[RWC_PHASE_INIT] += ev_ms(IEV);
-                st->phase_ms[RWC_PHASE_ACCUM] += ev_ms(IEV + 1);
+                st->phase_ms[RWC_PHASE_INIT] += ms_between(4 * Q, 4 * Q + 1);
+                st->phase_ms[RWC_PHASE_ACCUM] += ms_between(4 * Q + 2, 4 * Q + 3);
                 st->phase_launches[RWC_PHASE_INIT] += 1;
                 st->phase_launches[RWC_PHASE_ACCUM] += 1;
             }
@@ -540,7 +568,7 @@ static rwc_status sample_global(rwc_graph *G, uint64_t seed, int64_t tree0, int6
         st->draws = tot_marked;
         st->phase_units[RWC_PHASE_WALK] = tot_steps;
         st->phase_units[RWC_PHASE_CLASSIFY] = tot_marked;
-        st->phase_units[RWC_PHASE_FINISH] = tot_marked;
+        st->phase_units[RWC_PHASE_FINISH] = 0;
     }
     return RWC_OK;
 }
@@ -565,14 +593,19 @@ extern "C" rwc_status rwc_sample_trees(rwc_graph_t *G, uint64_t seed, int64_t tr
     const DevGraph &g = G->g;
     int mode = o.mode;
     if (mode == RWC_MODE_AUTO)
-        mode = (g.n <= 20000 && shared_bytes(g.n) <= 200 * 1024) ? RWC_MODE_SHARED : RWC_MODE_GLOBAL;
+        mode = (g.n <= 20000 && shared_bytes(g.n) <= 200 * 1024) ? RWC_MODE_SHARED : RWC_MODE_WALKER;
     if (mode == RWC_MODE_SHARED && (g.n > 32767 || shared_bytes(g.n) > 227 * 1024))
         return set_error(RWC_ERR_UNSUPPORTED, "shared mode needs n <= 20000");
     rwc_status s;
     try {
-        s = (mode == RWC_MODE_SHARED)
-                ? sample_shared(G, seed, tree0, T, sums, parents, visits, o, stats, (cudaStream_t)stream)
-                : sample_global(G, seed, tree0, T, sums, parents, visits, o, stats, (cudaStream_t)stream);
+        if (mode == RWC_MODE_SHARED)
+            s = sample_shared(G, seed, tree0, T, sums, parents, visits, o, stats, (cudaStream_t)stream);
+        else if (mode == RWC_MODE_WALKER)
+            s = sample_walker(G, seed, tree0, T, sums, parents, visits, o, stats, (cudaStream_t)stream);
+        else if (mode == RWC_MODE_GLOBAL)
+            s = sample_global(G, seed, tree0, T, sums, parents, visits, o, stats, (cudaStream_t)stream);
+        else
+            return set_error(RWC_ERR_INVALID, "unknown sampler mode %d", mode);
     } catch (const std::bad_alloc &) {
         return set_error(RWC_ERR_OOM, "host allocation failed");
     }

@@ -1,0 +1,422 @@
+// Asynchronous Wilson walkers (HBM mode for large graphs).
+//
+// Each tree is handled by one thread block whose threads are concurrent
+// Wilson walkers on the same successor stacks (Algorithm 3: a walk from a
+// start node follows RandomNeighbor until it reaches the tree, erasing loops).
+// Every vertex has one 64-bit word
+//     [ successor p : 32 | pop count k : 20 | owner : 12 ]
+// owner = FREE, SETTLED (in the tree) or the id of the walker whose current
+// loop-erased path contains the vertex; p caches succ(u, k) (or INVALID).
+// Operations, each a pop of a genuine cycle of the "top" graph or pure
+// bookkeeping, so by Wilson's cycle-popping theorem the final tree and every
+// k_u equal those of the sequential algorithm:
+//   claim   a FREE vertex x the head points to (64-bit CAS), draw p_x if
+//           needed, x becomes the head;
+//   pop     if the head points into the walker's own path, the loop from that
+//           vertex to the head is a cycle of the top graph: k++ on each of its
+//           vertices, all but the re-entered vertex become FREE;
+//   settle  if the head points to a SETTLED vertex the whole path joins the
+//           tree;
+//   yield   if the head points into another walker's path, the walker whose
+//           start comes later in the processing order releases its path
+//           (owners set to FREE, cached p kept) and requeues its start.
+// Waits are bounded; on exhaustion the block records an error and stops.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <random>
+#include <vector>
+
+#include "rwc_common.cuh"
+
+namespace rwc {
+namespace {
+
+constexpr uint32_t OWN_BITS = 12;
+constexpr uint64_t OWN_MASK = (1ull << OWN_BITS) - 1;
+constexpr uint32_t OWN_FREE = 0xFFF, OWN_SET = 0xFFE;
+constexpr uint32_t K_BITS = 20;
+constexpr uint64_t K_MAX = (1ull << K_BITS) - 1;
+constexpr uint32_t P_INVALID = 0xFFFFFFFFu;
+
+constexpr int WERR_KOVF = 1;     // a pop count exceeded 2^20 - 1
+constexpr int WERR_WAIT = 2;     // a bounded wait ran out
+constexpr int WERR_LOOP = 4;     // internal: a path walk exceeded n steps
+
+__device__ __forceinline__ uint32_t W_own(uint64_t w) { return (uint32_t)(w & OWN_MASK); }
+__device__ __forceinline__ uint32_t W_k(uint64_t w) { return (uint32_t)((w >> OWN_BITS) & K_MAX); }
+__device__ __forceinline__ uint32_t W_p(uint64_t w) { return (uint32_t)(w >> 32); }
+__device__ __forceinline__ uint64_t W_pack(uint32_t p, uint32_t k, uint32_t own) {
+    return ((uint64_t)p << 32) | ((uint64_t)k << OWN_BITS) | own;
+}
+__device__ __forceinline__ uint64_t ldv(const uint64_t *a) {
+    return *reinterpret_cast<const volatile uint64_t *>(a);
+}
+__device__ __forceinline__ void stv(uint64_t *a, uint64_t v) {
+    *reinterpret_cast<volatile uint64_t *>(a) = v;
+}
+
+struct WState {
+    uint64_t *word;        // [B][n]
+    int32_t *retry;        // [B][n-1] requeued start indices (circular)
+    const int32_t *order;  // [n-1] start order (a permutation of the non-root vertices)
+    int *err;
+    unsigned long long *ctr;   // [0] steps, [1] yields, [2] pops, [3] next tree
+};
+
+__global__ void w_init(int64_t n, int32_t root, uint64_t *word, int64_t B) {
+    const int64_t tot = B * n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u = i % n;
+        word[i] = (u == root) ? W_pack(P_INVALID, 0, OWN_SET) : W_pack(P_INVALID, 0, OWN_FREE);
+    }
+}
+
+// Walk a walker's path from s to h applying `own` to every vertex (FREE keeps
+// the cached successor, SET makes it final).  Returns false on a broken path.
+__device__ __forceinline__ bool path_set_owner(uint64_t *st, int32_t s, int32_t h, uint32_t me,
+                                               uint32_t own, int64_t n) {
+    int32_t y = s;
+    for (int64_t q = 0; q <= n; ++q) {
+        const uint64_t w = ldv(st + y);
+        if (W_own(w) != me) return false;
+        stv(st + y, (w & ~OWN_MASK) | own);
+        if (y == h) return true;
+        y = (int32_t)W_p(w);
+    }
+    return false;
+}
+
+// Retry queue: slots hold start index + 1 (0 = empty); a producer reserves a
+// slot with the tail counter and then fills it, a consumer reserves with the
+// head counter and waits (bounded) for the fill, then empties the slot.
+__device__ __forceinline__ void rq_push(int32_t *rq, int *tail, int64_t cap, int v) {
+    const int pos = atomicAdd(tail, 1);
+    *reinterpret_cast<volatile int32_t *>(rq + pos % cap) = v + 1;
+    __threadfence_block();
+}
+
+template <bool OFF64, bool WT>
+__global__ void __launch_bounds__(1024) w_trees(DevGraph g, WState s, int64_t B, uint32_t tree0,
+                                                uint32_t k0, uint32_t k1, int64_t max_wait) {
+    const int64_t n = g.n;
+    const int64_t nstart = n - 1;
+    const uint32_t me = threadIdx.x;
+    __shared__ int sh_tree;
+    __shared__ int sh_next;             // next fresh start index
+    __shared__ int sh_rhead, sh_rtail;  // retry queue
+    __shared__ int sh_active;           // walkers holding a start
+    __shared__ int sh_err;
+    extern __shared__ int sh[];         // prio[W], kill[W]
+    int *prio = sh;
+    int *kill = sh + blockDim.x;
+    unsigned long long steps = 0, yields = 0, pops = 0;
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            sh_tree = (int)atomicAdd(&s.ctr[3], 1ull);
+            sh_next = 0; sh_rhead = 0; sh_rtail = 0; sh_active = 0; sh_err = 0;
+        }
+        prio[threadIdx.x] = 0x7fffffff;
+        kill[threadIdx.x] = -1;
+        __syncthreads();
+        const int t = sh_tree;
+        if (t >= B) break;
+        uint64_t *st = s.word + (int64_t)t * n;
+        int32_t *rq = s.retry + (int64_t)t * nstart;
+        const uint32_t tree = tree0 + (uint32_t)t;
+
+        int32_t start = -1, head = -1;
+        int myprio = 0x7fffffff;
+        int64_t waited = 0;
+        unsigned backoff = 32;
+        for (;;) {
+            if (start < 0) {
+                // take a fresh start, else a requeued one; stop when nothing is
+                // left and no walker holds a start
+                int idx = -1;
+                if (*(volatile int *)&sh_next < nstart) {
+                    const int i = atomicAdd(&sh_next, 1);
+                    if (i < nstart) idx = i;
+                }
+                if (idx < 0) {
+                    const int hd = *(volatile int *)&sh_rhead;
+                    if (hd < *(volatile int *)&sh_rtail && atomicCAS(&sh_rhead, hd, hd + 1) == hd) {
+                        volatile int32_t *slot = rq + hd % nstart;
+                        int64_t q = 0;
+                        while (*slot == 0 && ++q < max_wait) __nanosleep(64);
+                        if (*slot == 0) { atomicOr(&sh_err, WERR_WAIT); break; }
+                        idx = *slot - 1;
+                        *slot = 0;
+                    }
+                }
+                if (idx < 0) {
+                    // done when no walker holds a start and both queues are empty
+                    const int act = *(volatile int *)&sh_active;
+                    __threadfence_block();
+                    if (act == 0 && *(volatile int *)&sh_rhead >= *(volatile int *)&sh_rtail &&
+                        *(volatile int *)&sh_next >= nstart)
+                        break;
+                    if (*(volatile int *)&sh_err) break;
+                    if (++waited > max_wait) { atomicOr(&sh_err, WERR_WAIT); break; }
+                    __nanosleep(1000);
+                    continue;
+                }
+                waited = 0;
+                const int32_t sv = s.order[idx];
+                if (W_own(ldv(st + sv)) == OWN_SET) continue;
+                start = sv; head = -1; myprio = idx;
+                atomicAdd(&sh_active, 1);
+                *(volatile int *)&prio[me] = idx;
+                backoff = 32;
+            }
+            if (*(volatile int *)&sh_err) break;
+            // a higher-priority walker asked this walk to yield
+            if (*(volatile int *)&kill[me] == myprio) {
+                *(volatile int *)&kill[me] = -1;
+                if (head >= 0 && !path_set_owner(st, start, head, me, OWN_FREE, n)) { atomicOr(&sh_err, WERR_LOOP); break; }
+                rq_push(rq, &sh_rtail, nstart, myprio);
+                ++yields;
+                *(volatile int *)&prio[me] = 0x7fffffff;
+                start = -1; head = -1;
+                atomicSub(&sh_active, 1);
+                continue;
+            }
+            const int32_t x = head < 0 ? start : (int32_t)W_p(ldv(st + head));
+            const uint64_t wx = ldv(st + x);
+            const uint32_t ox = W_own(wx);
+            ++steps;
+            if (ox == OWN_SET) {
+                if (head >= 0 && !path_set_owner(st, start, head, me, OWN_SET, n)) { atomicOr(&sh_err, WERR_LOOP); break; }
+                *(volatile int *)&prio[me] = 0x7fffffff;
+                start = -1; head = -1;
+                atomicSub(&sh_active, 1);
+                waited = 0;
+                continue;
+            }
+            if (ox == me) {
+                // loop x -> ... -> head -> x: pop it
+                int32_t y = x;
+                bool ok = false;
+                uint32_t kx = 0;
+                for (int64_t q = 0; q <= n; ++q) {
+                    const uint64_t wy = ldv(st + y);
+                    const int32_t nx = (int32_t)W_p(wy);
+                    const uint32_t k = W_k(wy) + 1u;
+                    if (k > K_MAX) { atomicOr(&sh_err, WERR_KOVF); break; }
+                    ++pops;
+                    if (y == x) kx = k;
+                    else stv(st + y, W_pack(P_INVALID, k, OWN_FREE));
+                    if (y == head) { ok = true; break; }
+                    y = nx;
+                }
+                if (!ok) { atomicOr(&sh_err, WERR_LOOP); break; }
+                const int32_t px = succ<OFF64, WT>(g, x, kx, tree, 0u, k0, k1);
+                stv(st + x, W_pack((uint32_t)px, kx, me));
+                head = x;
+                continue;
+            }
+            if (ox == OWN_FREE) {
+                const uint64_t claimed = (wx & ~OWN_MASK) | me;
+                if (atomicCAS((unsigned long long *)(st + x), (unsigned long long)wx,
+                              (unsigned long long)claimed) != wx)
+                    continue;
+                if (W_p(wx) == P_INVALID) {
+                    const int32_t px = succ<OFF64, WT>(g, x, W_k(wx), tree, 0u, k0, k1);
+                    stv(st + x, W_pack((uint32_t)px, W_k(wx), me));
+                }
+                head = x;
+                waited = 0;
+                backoff = 32;
+                continue;
+            }
+            // x belongs to another walker's path
+            const int op = *(volatile int *)&prio[ox];
+            if (myprio < op) {
+                *(volatile int *)&kill[ox] = op;   // the later walk yields
+                if (++waited > max_wait) { atomicOr(&sh_err, WERR_WAIT); break; }
+                __nanosleep(backoff);
+                backoff = min(backoff * 2u, 1024u);
+            } else {
+                if (head >= 0 && !path_set_owner(st, start, head, me, OWN_FREE, n)) { atomicOr(&sh_err, WERR_LOOP); break; }
+                rq_push(rq, &sh_rtail, nstart, myprio);
+                ++yields;
+                *(volatile int *)&prio[me] = 0x7fffffff;
+                start = -1; head = -1;
+                atomicSub(&sh_active, 1);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && sh_err) atomicOr(s.err, sh_err);
+        if (sh_err) break;
+    }
+    if (steps) atomicAdd(&s.ctr[0], steps);
+    if (yields) atomicAdd(&s.ctr[1], yields);
+    if (pops) atomicAdd(&s.ctr[2], pops);
+}
+
+// visits_u = k_u + 1 over the chunk's trees into sums; optional per-tree output.
+__global__ void w_accum(int64_t n, int32_t root, const uint64_t *word, int64_t B, double *sums,
+                        int32_t *parents, int32_t *visits, unsigned long long *draws) {
+    unsigned long long local = 0;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        int64_t acc = 0;
+        for (int64_t t = 0; t < B; ++t) {
+            const uint64_t w = word[t * n + u];
+            const int32_t vis = (u == root) ? 0 : (int32_t)W_k(w) + 1;
+            acc += vis;
+            if (parents) parents[t * n + u] = (u == root) ? -1 : (int32_t)W_p(w);
+            if (visits) visits[t * n + u] = vis;
+        }
+        local += (unsigned long long)acc;
+        if (sums && u != root) sums[u] += (double)acc;
+    }
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(draws, local);
+}
+
+template <class F>
+void dispatch(const DevGraph &g, F f) {
+    if (g.off64) {
+        if (g.weighted) f(std::true_type{}, std::true_type{});
+        else f(std::true_type{}, std::false_type{});
+    } else {
+        if (g.weighted) f(std::false_type{}, std::true_type{});
+        else f(std::false_type{}, std::false_type{});
+    }
+}
+
+}  // namespace
+
+// Start order shared by every tree of a graph: a fixed pseudo-random
+// permutation of the non-root vertices (the result does not depend on it).
+static rwc_status walker_order(rwc_graph *G, const int32_t **out) {
+    if (G->walk_order) { *out = G->walk_order; return RWC_OK; }
+    const int64_t n = G->g.n;
+    std::vector<int32_t> ord;
+    ord.reserve(n - 1);
+    for (int64_t u = 0; u < n; ++u)
+        if (u != G->g.root) ord.push_back((int32_t)u);
+    std::mt19937_64 rng(0x5eed5eedULL);
+    for (int64_t i = (int64_t)ord.size() - 1; i > 0; --i) {
+        const int64_t j = (int64_t)(rng() % (uint64_t)(i + 1));
+        std::swap(ord[i], ord[j]);
+    }
+    int32_t *d = nullptr;
+    RWC_CUDA_TRY(graph_alloc(G, (void **)&d, ord.size() * sizeof(int32_t)));
+    RWC_CUDA_TRY(cudaMemcpy(d, ord.data(), ord.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    G->walk_order = d;
+    *out = d;
+    return RWC_OK;
+}
+
+rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, double *sums,
+                         int32_t *parents, int32_t *visits, const rwc_options_t &o,
+                         rwc_stats_t *st, cudaStream_t stream) {
+    const DevGraph &g = G->g;
+    const int64_t n = g.n;
+    if (n >= ((int64_t)1 << 31) - 2) return set_error(RWC_ERR_UNSUPPORTED, "n too large for walker mode");
+    const int32_t *order = nullptr;
+    RWC_TRY(walker_order(G, &order));
+    int W = o.block_threads > 0 ? o.block_threads : (g.nnz / std::max<int64_t>(1, n) <= 6 ? 64 : 256);
+    W = std::max(32, std::min(1024, W / 32 * 32));
+    if (W > (int)OWN_SET) W = 1024;
+    const size_t per_tree = (size_t)n * (8 + 4) + 256;
+    int64_t B = o.trees_per_chunk;
+    if (B <= 0) {
+        size_t fr = 0, tot = 0;
+        RWC_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+        const size_t budget = o.memory_budget > 0 ? (size_t)o.memory_budget : (size_t)(fr * 0.6);
+        B = (int64_t)std::max<size_t>(1, budget / per_tree);
+    }
+    B = std::min(B, T);
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    void *buf = nullptr;
+    const size_t bytes = (size_t)B * n * 8 + (size_t)B * (n - 1) * 4 + 256;
+    RWC_CUDA_TRY(cudaMallocAsync(&buf, bytes, stream));
+    struct Free {
+        void *p; cudaStream_t s;
+        ~Free() { cudaFreeAsync(p, s); }
+    } fr{buf, stream};
+    WState ws;
+    ws.word = (uint64_t *)buf;
+    ws.retry = (int32_t *)((char *)buf + (size_t)B * n * 8);
+    char *tail = (char *)buf + (size_t)B * n * 8 + (size_t)B * (n - 1) * 4;
+    tail = (char *)(((uintptr_t)tail + 63) & ~(uintptr_t)63);
+    ws.order = order;
+    ws.err = (int *)tail;                                  // @0
+    ws.ctr = (unsigned long long *)(tail + 8);             // @8..40
+    unsigned long long *draws = (unsigned long long *)(tail + 40);
+    const bool prof = o.profile != 0;
+    cudaEvent_t ev[6] = {};
+    if (prof) for (auto &e : ev) cudaEventCreate(&e);
+    struct EvFree {
+        cudaEvent_t *e; bool on;
+        ~EvFree() { if (on) for (int i = 0; i < 6; ++i) cudaEventDestroy(e[i]); }
+    } evf{ev, prof};
+    const int64_t max_wait = (int64_t)1 << 26;   // ~ tens of seconds of backoff
+    const int sms = num_sms();
+    int64_t *h = G->host_scalars;
+    for (int64_t c0 = 0; c0 < T; c0 += B) {
+        const int64_t Bc = std::min(B, T - c0);
+        RWC_CUDA_TRY(cudaMemsetAsync(tail, 0, 64, stream));
+        RWC_CUDA_TRY(cudaMemsetAsync(ws.retry, 0, (size_t)Bc * (n - 1) * 4, stream));
+        if (prof) cudaEventRecord(ev[0], stream);
+        ::rwc::count_launches(1);
+        w_init<<<sms * 8, 256, 0, stream>>>(n, g.root, ws.word, Bc);
+        if (prof) cudaEventRecord(ev[1], stream);
+        rwc_status status = RWC_OK;
+        dispatch(g, [&](auto off64, auto wt) {
+            auto kern = w_trees<decltype(off64)::value, decltype(wt)::value>;
+            const size_t smem = 2 * (size_t)W * sizeof(int);
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W, smem);
+            if (per_sm < 1) { status = set_error(RWC_ERR_UNSUPPORTED, "walker block does not fit"); return; }
+            const int64_t blocks = std::min<int64_t>(Bc, (int64_t)sms * per_sm);
+            ::rwc::count_launches(1);
+            kern<<<(unsigned)blocks, W, smem, stream>>>(g, ws, Bc, (uint32_t)(tree0 + c0), k0, k1, max_wait);
+        });
+        RWC_TRY(status);
+        if (prof) cudaEventRecord(ev[2], stream);
+        ::rwc::count_launches(1);
+        w_accum<<<sms * 8, 256, 0, stream>>>(n, g.root, ws.word, Bc, sums,
+                                             parents ? parents + c0 * n : nullptr,
+                                             visits ? visits + c0 * n : nullptr, draws);
+        if (prof) cudaEventRecord(ev[3], stream);
+        RWC_CUDA_TRY(cudaGetLastError());
+        RWC_CUDA_TRY(cudaMemcpyAsync(h, tail, 48, cudaMemcpyDeviceToHost, stream));
+        RWC_CUDA_TRY(cudaStreamSynchronize(stream));
+        const int e = (int)(h[0] & 0xffffffff);
+        if (e & WERR_KOVF) return set_error(RWC_ERR_UNSUPPORTED, "a vertex was popped more than 2^20 - 1 times");
+        if (e & WERR_LOOP) return set_error(RWC_ERR_CUDA, "walker internal check failed");
+        if (e & WERR_WAIT) return set_error(RWC_ERR_NOT_CONVERGED, "a walker wait exceeded its bound");
+        if (st) {
+            st->chunks += 1;
+            st->walk_steps += h[1];
+            st->rounds += h[2];          // yields (re-queued walks)
+            st->draws += h[5];
+            st->marked += h[5];
+            st->phase_units[RWC_PHASE_INIT] += Bc * n;
+            st->phase_units[RWC_PHASE_WALK] += h[1];
+            st->phase_units[RWC_PHASE_ACCUM] += Bc * n;
+            if (prof) {
+                float a = 0, b2 = 0, c = 0;
+                cudaEventElapsedTime(&a, ev[0], ev[1]);
+                cudaEventElapsedTime(&b2, ev[1], ev[2]);
+                cudaEventElapsedTime(&c, ev[2], ev[3]);
+                st->phase_ms[RWC_PHASE_INIT] += a;
+                st->phase_ms[RWC_PHASE_WALK] += b2;
+                st->phase_ms[RWC_PHASE_ACCUM] += c;
+                st->phase_launches[RWC_PHASE_INIT] += 1;
+                st->phase_launches[RWC_PHASE_WALK] += 1;
+                st->phase_launches[RWC_PHASE_ACCUM] += 1;
+            }
+        }
+    }
+    if (st) st->mode = RWC_MODE_WALKER;
+    return RWC_OK;
+}
+
+}  // namespace rwc

@@ -43,7 +43,10 @@ SPECIAL = {
 MODES = {"shared": rwc.Options(mode=rwc.MODE_SHARED),
          "global": rwc.Options(mode=rwc.MODE_GLOBAL),
          "global_nojump": rwc.Options(mode=rwc.MODE_GLOBAL, use_jumps=0),
-         "global_chunk3": rwc.Options(mode=rwc.MODE_GLOBAL, trees_per_chunk=3)}
+         "global_chunk3": rwc.Options(mode=rwc.MODE_GLOBAL, trees_per_chunk=3),
+         "walker": rwc.Options(mode=rwc.MODE_WALKER),
+         "walker_w32_chunk5": rwc.Options(mode=rwc.MODE_WALKER, block_threads=32, trees_per_chunk=5),
+         "walker_w1024": rwc.Options(mode=rwc.MODE_WALKER, block_threads=1024)}
 
 
 @pytest.mark.parametrize("mode", list(MODES))
@@ -52,20 +55,26 @@ def test_special_graphs_bit_exact(gname, mode):
     assert_exact(SPECIAL[gname](), 37, MODES[mode])
 
 
-@pytest.mark.parametrize("mode", ["shared", "global", "global_chunk3"])
+@pytest.mark.parametrize("mode", ["shared", "global", "global_chunk3", "walker", "walker_w32_chunk5"])
 def test_small_ba_config_bit_exact(mode):
     """BA n=2000, 3 edges per node + Hamiltonian path, unit weights, 1000
     trees, Philox seed 1: every tree identical to the oracle's."""
     g = synth.ba(2000, 3, seed=0)
     opt = MODES[mode] if mode != "global_chunk3" else rwc.Options(mode=rwc.MODE_GLOBAL, trees_per_chunk=333)
+    if mode == "walker_w32_chunk5":
+        opt = rwc.Options(mode=rwc.MODE_WALKER, block_threads=32, trees_per_chunk=337)
     assert_exact(g, 1000, opt)
 
 
-@pytest.mark.parametrize("mode", ["global", "global_nojump"])
+@pytest.mark.parametrize("mode", ["global", "global_nojump", "walker", "walker_w64"])
 def test_grid_several_chunks_bit_exact(mode):
     g = synth.grid2d(61, 67)
-    opt = rwc.Options(mode=rwc.MODE_GLOBAL, trees_per_chunk=9,
-                      use_jumps=0 if mode == "global_nojump" else -1)
+    if mode.startswith("walker"):
+        opt = rwc.Options(mode=rwc.MODE_WALKER, trees_per_chunk=9,
+                          block_threads=64 if mode == "walker_w64" else 0)
+    else:
+        opt = rwc.Options(mode=rwc.MODE_GLOBAL, trees_per_chunk=9,
+                          use_jumps=0 if mode == "global_nojump" else -1)
     assert_exact(g, 23, opt, root=-1)
 
 
@@ -73,6 +82,8 @@ def test_weighted_rmat_int64_offsets_bit_exact():
     g = synth.rmat(12, 16, seed=3, sigma=1.0)
     assert_exact(g, 16, rwc.Options(mode=rwc.MODE_GLOBAL), flags=rwc.GRAPH_INT64_OFFSETS)
     assert_exact(g, 8, rwc.Options(mode=rwc.MODE_GLOBAL))
+    assert_exact(g, 16, rwc.Options(mode=rwc.MODE_WALKER), flags=rwc.GRAPH_INT64_OFFSETS)
+    assert_exact(g, 16, rwc.Options(mode=rwc.MODE_WALKER, block_threads=128))
 
 
 def test_weighted_rgg_shared_bit_exact():
@@ -88,6 +99,7 @@ def test_tree_offset_and_shards_add_up():
     G.sample(30, seed=9, tree0=20, sums=b)
     assert torch.equal(a, b)
     assert_exact(g, 10, rwc.Options(mode=rwc.MODE_GLOBAL), seed=9, tree0=4000000000)
+    assert_exact(g, 10, rwc.Options(mode=rwc.MODE_WALKER), seed=9, tree0=4000000000)
 
 
 def test_seed_high_bits_matter():
@@ -113,6 +125,7 @@ def test_max_rounds_reports_not_converged():
         assert e.value.status == 4
         # the handle stays usable afterwards
         assert_exact(g, 3, rwc.Options(mode=mode))
+    assert_exact(g, 3, rwc.Options(mode=rwc.MODE_WALKER))
 
 
 def _check_tree(g, root, par):

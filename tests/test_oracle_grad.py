@@ -58,3 +58,14 @@ def test_sketch_is_unbiased():
         acc += grad.grad_sketch(g.n, a, b, w, c, Q)
     mean = acc / R
     assert np.abs(mean - gc).max() < 0.05 * np.abs(gc).max()
+
+
+def test_sparse_sketch_route_matches_dense_sketch():
+    g = synth.rgg(120, 9.0, seed=8, sigma=0.5)
+    a, b, w = _edges(g)
+    c = synth.uniform_vector(g.n, 8)
+    Q = np.random.default_rng(3).choice([-1.0, 1.0], size=(8, g.n)) / np.sqrt(8)
+    dense = grad.grad_sketch(g.n, a, b, w, c, Q)
+    sel = np.arange(0, len(a), 7)
+    sparse = grad.grad_sketch_sparse(g.n, a, b, w, c, Q, sel)
+    assert np.allclose(sparse, dense[sel], rtol=1e-8, atol=1e-8 * np.abs(dense).max())
