@@ -41,16 +41,22 @@ WORKLOADS = {
     "rmat24": [("rmat24", 500)],
 }
 
-# Algorithmic bytes per work unit of each sampler phase:
-# WALK: read a vertex's successor and tag (8 B) per pointer-chasing step;
-# POP: per successor draw, row bounds (8 B, int32 offsets; 16 B int64) + arc
-# (4 B unit weight, 16 B alias record) + successor/pop-count update (12 B).
 PHASE_NAMES = ("init", "walk", "classify", "pop", "finish", "accum")
+KERNEL_NAMES = {1: {"init": "g_init", "walk": "g_walk", "pop": "g_pop", "accum": "g_accum"},
+                2: {"walk": "s_trees"},
+                3: {"init": "w_init", "walk": "w_trees", "accum": "w_accum"}}
 
 
-def bytes_per_unit(phase, weighted, off64):
+def bytes_per_unit(phase, mode, weighted, off64):
+    """Algorithmic bytes per work unit of each sampler phase.
+    mode: 1 round-based (GLOBAL), 2 shared memory, 3 concurrent walkers."""
     row = 16 if off64 else 8
     arc = 16 if weighted else 4
+    if mode == 3:   # walker kernel: per draw, row bounds + arc + state word read/write
+        return {"init": 8, "walk": row + arc + 16, "classify": 0, "pop": 0, "finish": 0,
+                "accum": 8}[phase]
+    if mode == 2:   # shared memory: per draw, the graph reads only
+        return {"init": 0, "walk": row + arc, "classify": 0, "pop": 0, "finish": 0, "accum": 0}[phase]
     return {"init": row + arc + 12, "walk": 8, "classify": 5, "pop": row + arc + 12,
             "finish": 9, "accum": 12}[phase]
 
@@ -297,15 +303,19 @@ def main():
             phase_ms[p] += st["phase_ms"][i]
             phase_units[p] += st["phase_units"][i]
             phase_launch[p] += st["phase_launches"][i]
-            phase_bytes[p] += st["phase_units"][i] * bytes_per_unit(p, bool(info.weighted), bool(info.offsets64))
+            phase_bytes[p] += st["phase_units"][i] * bytes_per_unit(p, st["mode"], bool(info.weighted),
+                                                                    bool(info.offsets64))
             sampler_ms += st["phase_ms"][i]
     dom = max(PHASE_NAMES, key=lambda p: phase_ms[p])
+    dom_mode = all_stats[-1][1]["mode"] if all_stats else 0
     nl = max(1, phase_launch[dom])
     per_launch_bytes = phase_bytes[dom] / nl
     per_launch_s = phase_ms[dom] / 1000.0 / nl
     achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None, "kernel": f"g_{dom}",
+                "frac": achieved / hbm_peak, "traffic": None,
+                "kernel": KERNEL_NAMES.get(dom_mode, {}).get(dom, dom),
+                "unit_bytes": bytes_per_unit(dom, dom_mode, False, False),
                 "peak_source": f"{peak_src} hbm_gbs",
                 "phase_share": {p: phase_ms[p] / max(sampler_ms, 1e-9) for p in PHASE_NAMES}}
 

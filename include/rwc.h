@@ -108,8 +108,9 @@ typedef struct {
     int32_t reserved;
     int64_t marked;       /* compressed-graph nodes over all rounds (= draws) */
     /* with rwc_options_t.profile: device time (ms), launches and work units
-     * per phase; units are vertices (INIT, ACCUM), walk steps (WALK), marked
-     * entries (CLASSIFY, FINISH) and successor draws (POP). */
+     * per phase; units are vertices (INIT, ACCUM), pointer-chasing steps (WALK
+     * in GLOBAL mode), successor draws (POP in GLOBAL mode; WALK in WALKER and
+     * SHARED modes) and marked entries (CLASSIFY). */
     double phase_ms[RWC_NPHASE];
     int64_t phase_launches[RWC_NPHASE];
     int64_t phase_units[RWC_NPHASE];

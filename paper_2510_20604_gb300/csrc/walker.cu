@@ -20,6 +20,10 @@
 //   yield   if the head points into another walker's path, the walker whose
 //           start comes later in the processing order releases its path
 //           (owners set to FREE, cached p kept) and requeues its start.
+// A walker that yielded takes no new start until the walker it yielded to
+// has changed state (every walker publishes a version counter), so the
+// earlier walk always gets the contested vertex first.  The earliest active
+// walk never yields, so the block always makes progress.
 // Waits are bounded; on exhaustion the block records an error and stops.
 #include <algorithm>
 #include <cstring>
@@ -108,9 +112,11 @@ __global__ void __launch_bounds__(1024) w_trees(DevGraph g, WState s, int64_t B,
     __shared__ int sh_rhead, sh_rtail;  // retry queue
     __shared__ int sh_active;           // walkers holding a start
     __shared__ int sh_err;
-    extern __shared__ int sh[];         // prio[W], kill[W]
+    extern __shared__ int sh[];         // prio[W], kill[W], killer[W], ver[W]
     int *prio = sh;
     int *kill = sh + blockDim.x;
+    int *killer = sh + 2 * blockDim.x;
+    int *ver = sh + 3 * blockDim.x;
     unsigned long long steps = 0, yields = 0, pops = 0;
 
     for (;;) {
@@ -120,6 +126,8 @@ __global__ void __launch_bounds__(1024) w_trees(DevGraph g, WState s, int64_t B,
         }
         prio[threadIdx.x] = 0x7fffffff;
         kill[threadIdx.x] = -1;
+        killer[threadIdx.x] = -1;
+        ver[threadIdx.x] = 0;
         __syncthreads();
         const int t = sh_tree;
         if (t >= B) break;
@@ -131,7 +139,22 @@ __global__ void __launch_bounds__(1024) w_trees(DevGraph g, WState s, int64_t B,
         int myprio = 0x7fffffff;
         int64_t waited = 0;
         unsigned backoff = 32;
+        int wait_on = -1, wait_ver = 0;   // after a yield: the walker yielded to
+        auto bump = [&]() { *(volatile int *)&ver[me] = ver[me] + 1; };
         for (;;) {
+            if (start < 0 && wait_on >= 0) {
+                // wait while the walker yielded to still holds its start and has
+                // not changed state
+                if (*(volatile int *)&ver[wait_on] == wait_ver &&
+                    *(volatile int *)&prio[wait_on] != 0x7fffffff) {
+                    if (*(volatile int *)&sh_err) break;
+                    if (++waited > max_wait) { atomicOr(&sh_err, WERR_WAIT); break; }
+                    __nanosleep(64);
+                    continue;
+                }
+                wait_on = -1;
+                waited = 0;
+            }
             if (start < 0) {
                 // take a fresh start, else a requeued one; stop when nothing is
                 // left and no walker holds a start
@@ -169,16 +192,20 @@ __global__ void __launch_bounds__(1024) w_trees(DevGraph g, WState s, int64_t B,
                 start = sv; head = -1; myprio = idx;
                 atomicAdd(&sh_active, 1);
                 *(volatile int *)&prio[me] = idx;
+                bump();
                 backoff = 32;
             }
             if (*(volatile int *)&sh_err) break;
             // a higher-priority walker asked this walk to yield
             if (*(volatile int *)&kill[me] == myprio) {
+                const int kb = *(volatile int *)&killer[me];
                 *(volatile int *)&kill[me] = -1;
                 if (head >= 0 && !path_set_owner(st, start, head, me, OWN_FREE, n)) { atomicOr(&sh_err, WERR_LOOP); break; }
+                if (kb >= 0) { wait_on = kb; wait_ver = *(volatile int *)&ver[kb]; }
                 rq_push(rq, &sh_rtail, nstart, myprio);
                 ++yields;
                 *(volatile int *)&prio[me] = 0x7fffffff;
+                bump();
                 start = -1; head = -1;
                 atomicSub(&sh_active, 1);
                 continue;
@@ -190,6 +217,7 @@ __global__ void __launch_bounds__(1024) w_trees(DevGraph g, WState s, int64_t B,
             if (ox == OWN_SET) {
                 if (head >= 0 && !path_set_owner(st, start, head, me, OWN_SET, n)) { atomicOr(&sh_err, WERR_LOOP); break; }
                 *(volatile int *)&prio[me] = 0x7fffffff;
+                bump();
                 start = -1; head = -1;
                 atomicSub(&sh_active, 1);
                 waited = 0;
@@ -215,6 +243,7 @@ __global__ void __launch_bounds__(1024) w_trees(DevGraph g, WState s, int64_t B,
                 const int32_t px = succ<OFF64, WT>(g, x, kx, tree, 0u, k0, k1);
                 stv(st + x, W_pack((uint32_t)px, kx, me));
                 head = x;
+                bump();
                 continue;
             }
             if (ox == OWN_FREE) {
@@ -227,6 +256,7 @@ __global__ void __launch_bounds__(1024) w_trees(DevGraph g, WState s, int64_t B,
                     stv(st + x, W_pack((uint32_t)px, W_k(wx), me));
                 }
                 head = x;
+                bump();
                 waited = 0;
                 backoff = 32;
                 continue;
@@ -234,15 +264,20 @@ __global__ void __launch_bounds__(1024) w_trees(DevGraph g, WState s, int64_t B,
             // x belongs to another walker's path
             const int op = *(volatile int *)&prio[ox];
             if (myprio < op) {
+                *(volatile int *)&killer[ox] = (int)me;
+                __threadfence_block();
                 *(volatile int *)&kill[ox] = op;   // the later walk yields
                 if (++waited > max_wait) { atomicOr(&sh_err, WERR_WAIT); break; }
                 __nanosleep(backoff);
                 backoff = min(backoff * 2u, 1024u);
             } else {
                 if (head >= 0 && !path_set_owner(st, start, head, me, OWN_FREE, n)) { atomicOr(&sh_err, WERR_LOOP); break; }
+                wait_on = (int)ox;
+                wait_ver = *(volatile int *)&ver[ox];
                 rq_push(rq, &sh_rtail, nstart, myprio);
                 ++yields;
                 *(volatile int *)&prio[me] = 0x7fffffff;
+                bump();
                 start = -1; head = -1;
                 atomicSub(&sh_active, 1);
             }
@@ -370,7 +405,7 @@ rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, 
         rwc_status status = RWC_OK;
         dispatch(g, [&](auto off64, auto wt) {
             auto kern = w_trees<decltype(off64)::value, decltype(wt)::value>;
-            const size_t smem = 2 * (size_t)W * sizeof(int);
+            const size_t smem = 4 * (size_t)W * sizeof(int);
             int per_sm = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W, smem);
             if (per_sm < 1) { status = set_error(RWC_ERR_UNSUPPORTED, "walker block does not fit"); return; }
@@ -399,7 +434,7 @@ rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, 
             st->draws += h[5];
             st->marked += h[5];
             st->phase_units[RWC_PHASE_INIT] += Bc * n;
-            st->phase_units[RWC_PHASE_WALK] += h[1];
+            st->phase_units[RWC_PHASE_WALK] += h[5];   // successor draws
             st->phase_units[RWC_PHASE_ACCUM] += Bc * n;
             if (prof) {
                 float a = 0, b2 = 0, c = 0;
