@@ -38,6 +38,8 @@ WORKLOADS = {
     "grid1024": [("grid1024", 2000)],
     "rmat20": [("rmat20", 2000)],
     "ba2000": [("ba2000", 1000)],
+    "grid512": [("grid512", 64)],
+    "rmat18": [("rmat18", 512)],
     "rmat24": [("rmat24", 500)],
 }
 
@@ -65,8 +67,12 @@ def make_graph(key):
     import synth
     if key == "grid1024":
         return synth.grid2d(1024, 1024)
+    if key == "grid512":
+        return synth.grid2d(512, 512)
     if key == "rmat20":
         return synth.rmat(20, 16, seed=0)
+    if key == "rmat18":
+        return synth.rmat(18, 16, seed=0)
     if key == "rmat24":
         return synth.rmat(24, 16, seed=0, sigma=1.0)
     if key == "ba2000":
@@ -196,6 +202,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=20.0)
+    ap.add_argument("--walkers", type=int, default=0, help="walkers per tree (0 = auto)")
     args = ap.parse_args()
     if args.trees:
         WORKLOADS[args.workload] = [(k, args.trees) for k, _ in WORKLOADS[args.workload]]
@@ -226,7 +233,7 @@ def main():
         sums = torch.zeros(g.n, dtype=torch.float64, device=dev)
         graphs.append((key, T, g, G, sums))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    opt = rwc.Options(profile=1)
+    opt = rwc.Options(profile=1, block_threads=args.walkers)
     tree_base = rank * 10_000_000
 
     def step(stats_out=None):
@@ -393,8 +400,9 @@ def main():
             "clocks": clk,
             "wall_s_timed": t_wall,
             "step_ms": step_ms,
-            "sampler_stats": [{"graph": k, "rounds": st["rounds"], "draws": st["draws"],
-                               "walk_steps": st["walk_steps"], "chunks": st["chunks"]}
+            "sampler_stats": [{"graph": k, "mode": st["mode"], "rounds_or_yields": st["rounds"],
+                               "draws": st["draws"], "walk_steps": st["walk_steps"],
+                               "chunks": st["chunks"], "diag": st["diag"]}
                               for k, st in all_stats[-len(graphs):]],
         }
         print(json.dumps(line), flush=True)

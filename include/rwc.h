@@ -114,6 +114,10 @@ typedef struct {
     double phase_ms[RWC_NPHASE];
     int64_t phase_launches[RWC_NPHASE];
     int64_t phase_units[RWC_NPHASE];
+    /* diagnostics; WALKER mode: loop iterations summed over all walkers in
+     * the states idle, walk, pop, release, settle, wait-for-yield,
+     * wait-after-yield */
+    int64_t diag[8];
 } rwc_stats_t;
 
 /* Message describing the last error on the calling thread ("" if none). */

@@ -47,7 +47,7 @@ class Stats(ctypes.Structure):
                 ("walk_steps", ctypes.c_int64), ("chunks", ctypes.c_int64), ("mode", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("marked", ctypes.c_int64),
                 ("phase_ms", ctypes.c_double * NPHASE), ("phase_launches", ctypes.c_int64 * NPHASE),
-                ("phase_units", ctypes.c_int64 * NPHASE)]
+                ("phase_units", ctypes.c_int64 * NPHASE), ("diag", ctypes.c_int64 * 8)]
 
     def as_dict(self):
         out = {}
@@ -55,7 +55,7 @@ class Stats(ctypes.Structure):
             if f == "reserved":
                 continue
             v = getattr(self, f)
-            out[f] = list(v) if f.startswith("phase_") else v
+            out[f] = list(v) if (f.startswith("phase_") or f == "diag") else v
         return out
 
 

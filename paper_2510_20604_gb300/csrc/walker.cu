@@ -53,11 +53,28 @@ __device__ __forceinline__ uint32_t W_p(uint64_t w) { return (uint32_t)(w >> 32)
 __device__ __forceinline__ uint64_t W_pack(uint32_t p, uint32_t k, uint32_t own) {
     return ((uint64_t)p << 32) | ((uint64_t)k << OWN_BITS) | own;
 }
+// Every access to a tree's state comes from the one thread block that owns
+// the tree, so block-scope relaxed loads, stores and CAS are enough (kernel
+// boundaries order them with the init and accumulation kernels).
 __device__ __forceinline__ uint64_t ldv(const uint64_t *a) {
-    return *reinterpret_cast<const volatile uint64_t *>(a);
+    uint64_t v;
+    asm volatile("ld.relaxed.cta.global.u64 %0, [%1];" : "=l"(v) : "l"(a) : "memory");
+    return v;
 }
 __device__ __forceinline__ void stv(uint64_t *a, uint64_t v) {
-    *reinterpret_cast<volatile uint64_t *>(a) = v;
+    asm volatile("st.relaxed.cta.global.u64 [%0], %1;" ::"l"(a), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t cas_cta(uint64_t *a, uint64_t cmp, uint64_t val) {
+    return atomicCAS_block(reinterpret_cast<unsigned long long *>(a), (unsigned long long)cmp,
+                           (unsigned long long)val);
+}
+__device__ __forceinline__ int32_t ld32(const int32_t *a) {
+    int32_t v;
+    asm volatile("ld.relaxed.cta.global.s32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st32(int32_t *a, int32_t v) {
+    asm volatile("st.relaxed.cta.global.s32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
 }
 
 struct WState {
@@ -66,6 +83,7 @@ struct WState {
     const int32_t *order;  // [n-1] start order (a permutation of the non-root vertices)
     int *err;
     unsigned long long *ctr;   // [0] steps, [1] yields, [2] pops, [3] next tree
+    unsigned long long *diag;  // [8] loop iterations per walker state
 };
 
 __global__ void w_init(int64_t n, int32_t root, uint64_t *word, int64_t B) {
@@ -97,37 +115,52 @@ __device__ __forceinline__ bool path_set_owner(uint64_t *st, int32_t s, int32_t 
 // head counter and waits (bounded) for the fill, then empties the slot.
 __device__ __forceinline__ void rq_push(int32_t *rq, int *tail, int64_t cap, int v) {
     const int pos = atomicAdd(tail, 1);
-    *reinterpret_cast<volatile int32_t *>(rq + pos % cap) = v + 1;
+    st32(rq + pos % cap, v + 1);
     __threadfence_block();
 }
 
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Walker states.  Each loop iteration does at most one vertex of work, so
+// the lanes of a warp stay close to each other in the loop; waits poll
+// shared memory only.
+enum : int { S_IDLE = 0, S_WALK, S_POP, S_REL, S_SET, S_WAITK, S_WAITV, S_DONE };
+
 template <bool OFF64, bool WT>
 __global__ void __launch_bounds__(1024) w_trees(DevGraph g, WState s, int64_t B, uint32_t tree0,
-                                                uint32_t k0, uint32_t k1, int64_t max_wait) {
+                                                uint32_t k0, uint32_t k1, int64_t max_wait_ns) {
     const int64_t n = g.n;
     const int64_t nstart = n - 1;
     const uint32_t me = threadIdx.x;
+    constexpr int INF = 0x7fffffff;
     __shared__ int sh_tree;
     __shared__ int sh_next;             // next fresh start index
     __shared__ int sh_rhead, sh_rtail;  // retry queue
     __shared__ int sh_active;           // walkers holding a start
     __shared__ int sh_err;
-    extern __shared__ int sh[];         // prio[W], kill[W], killer[W], ver[W]
+    extern __shared__ int sh[];         // prio[W], kill[W], killer[W], ver[W], killv[W]
     int *prio = sh;
     int *kill = sh + blockDim.x;
     int *killer = sh + 2 * blockDim.x;
     int *ver = sh + 3 * blockDim.x;
+    int *killv = sh + 4 * blockDim.x;   // the contested vertex of a yield request
     unsigned long long steps = 0, yields = 0, pops = 0;
+    unsigned long long it_state[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 
     for (;;) {
         if (threadIdx.x == 0) {
             sh_tree = (int)atomicAdd(&s.ctr[3], 1ull);
             sh_next = 0; sh_rhead = 0; sh_rtail = 0; sh_active = 0; sh_err = 0;
         }
-        prio[threadIdx.x] = 0x7fffffff;
+        prio[threadIdx.x] = INF;
         kill[threadIdx.x] = -1;
         killer[threadIdx.x] = -1;
         ver[threadIdx.x] = 0;
+        killv[threadIdx.x] = -1;
         __syncthreads();
         const int t = sh_tree;
         if (t >= B) break;
@@ -135,152 +168,225 @@ __global__ void __launch_bounds__(1024) w_trees(DevGraph g, WState s, int64_t B,
         int32_t *rq = s.retry + (int64_t)t * nstart;
         const uint32_t tree = tree0 + (uint32_t)t;
 
-        int32_t start = -1, head = -1;
-        int myprio = 0x7fffffff;
-        int64_t waited = 0;
-        unsigned backoff = 32;
-        int wait_on = -1, wait_ver = 0;   // after a yield: the walker yielded to
+        int state = S_IDLE;
+        int32_t start = -1, head = -1, hp = -1, cur = -1, popx = -1;
+        int32_t cut = -1;             // release: suffix from `cut` first, then the prefix
+        uint32_t kx = 0;
+        int myprio = INF, wait_on = -1, wait_ver = 0, wait_prio = 0;
+        int64_t walked = 0;          // vertices visited in the current POP/REL/SET pass
+        int64_t polls = 0;
+        uint64_t wait_t0 = 0;
+        auto vread = [](const int *a) { return *(const volatile int *)a; };
         auto bump = [&]() { *(volatile int *)&ver[me] = ver[me] + 1; };
-        for (;;) {
-            if (start < 0 && wait_on >= 0) {
-                // wait while the walker yielded to still holds its start and has
-                // not changed state
-                if (*(volatile int *)&ver[wait_on] == wait_ver &&
-                    *(volatile int *)&prio[wait_on] != 0x7fffffff) {
-                    if (*(volatile int *)&sh_err) break;
-                    if (++waited > max_wait) { atomicOr(&sh_err, WERR_WAIT); break; }
-                    __nanosleep(64);
-                    continue;
-                }
-                wait_on = -1;
-                waited = 0;
+        // returns true when the current wait has exceeded its time bound
+        auto waited_out = [&]() {
+            if (polls++ == 0) wait_t0 = gtimer();
+            if ((polls & 1023) == 0 && gtimer() - wait_t0 > (uint64_t)max_wait_ns) {
+                atomicOr(&sh_err, WERR_WAIT);
+                return true;
             }
-            if (start < 0) {
-                // take a fresh start, else a requeued one; stop when nothing is
-                // left and no walker holds a start
+            return false;
+        };
+        auto drop_start = [&](bool requeue) {
+            if (requeue) {
+                rq_push(rq, &sh_rtail, nstart, myprio);
+                ++yields;
+            }
+            *(volatile int *)&prio[me] = INF;
+            bump();
+            start = -1; head = -1;
+            atomicSub(&sh_active, 1);
+            polls = 0;
+        };
+        // Lockstep: every iteration starts with a warp vote, so the 32 walkers
+        // of a warp each do one step per iteration (their memory accesses
+        // overlap) and a waiting walker polls once per iteration instead of
+        // spinning ahead of the others.  Finished walkers idle until the whole
+        // warp is done; errors end the loop for everyone through the vote.
+        for (;;) {
+            const bool err = vread(&sh_err) != 0;
+            if (__any_sync(0xffffffffu, err)) break;
+            if (__all_sync(0xffffffffu, state == S_DONE)) break;
+            if (state == S_DONE) continue;
+            ++it_state[state];
+            do {
+            if (state == S_IDLE) {
+                // a fresh start, else a requeued one
                 int idx = -1;
-                if (*(volatile int *)&sh_next < nstart) {
+                if (vread(&sh_next) < nstart) {
                     const int i = atomicAdd(&sh_next, 1);
                     if (i < nstart) idx = i;
                 }
                 if (idx < 0) {
-                    const int hd = *(volatile int *)&sh_rhead;
-                    if (hd < *(volatile int *)&sh_rtail && atomicCAS(&sh_rhead, hd, hd + 1) == hd) {
-                        volatile int32_t *slot = rq + hd % nstart;
-                        int64_t q = 0;
-                        while (*slot == 0 && ++q < max_wait) __nanosleep(64);
-                        if (*slot == 0) { atomicOr(&sh_err, WERR_WAIT); break; }
-                        idx = *slot - 1;
-                        *slot = 0;
+                    const int hd = vread(&sh_rhead);
+                    if (hd < vread(&sh_rtail) && atomicCAS(&sh_rhead, hd, hd + 1) == hd) {
+                        int32_t *slot = rq + hd % nstart;
+                        uint64_t t0 = gtimer();
+                        int32_t v = ld32(slot);
+                        while (v == 0 && gtimer() - t0 < (uint64_t)max_wait_ns) v = ld32(slot);
+                        if (v == 0) { atomicOr(&sh_err, WERR_WAIT); break; }
+                        idx = v - 1;
+                        st32(slot, 0);
                     }
                 }
                 if (idx < 0) {
-                    // done when no walker holds a start and both queues are empty
-                    const int act = *(volatile int *)&sh_active;
+                    const int act = vread(&sh_active);
                     __threadfence_block();
-                    if (act == 0 && *(volatile int *)&sh_rhead >= *(volatile int *)&sh_rtail &&
-                        *(volatile int *)&sh_next >= nstart)
+                    if (act == 0 && vread(&sh_rhead) >= vread(&sh_rtail) && vread(&sh_next) >= nstart)
+                        state = S_DONE;
+                    else if (waited_out())
                         break;
-                    if (*(volatile int *)&sh_err) break;
-                    if (++waited > max_wait) { atomicOr(&sh_err, WERR_WAIT); break; }
-                    __nanosleep(1000);
                     continue;
                 }
-                waited = 0;
+                polls = 0;
                 const int32_t sv = s.order[idx];
                 if (W_own(ldv(st + sv)) == OWN_SET) continue;
                 start = sv; head = -1; myprio = idx;
                 atomicAdd(&sh_active, 1);
                 *(volatile int *)&prio[me] = idx;
                 bump();
-                backoff = 32;
-            }
-            if (*(volatile int *)&sh_err) break;
-            // a higher-priority walker asked this walk to yield
-            if (*(volatile int *)&kill[me] == myprio) {
-                const int kb = *(volatile int *)&killer[me];
-                *(volatile int *)&kill[me] = -1;
-                if (head >= 0 && !path_set_owner(st, start, head, me, OWN_FREE, n)) { atomicOr(&sh_err, WERR_LOOP); break; }
-                if (kb >= 0) { wait_on = kb; wait_ver = *(volatile int *)&ver[kb]; }
-                rq_push(rq, &sh_rtail, nstart, myprio);
-                ++yields;
-                *(volatile int *)&prio[me] = 0x7fffffff;
-                bump();
-                start = -1; head = -1;
-                atomicSub(&sh_active, 1);
+                state = S_WALK;
                 continue;
             }
-            const int32_t x = head < 0 ? start : (int32_t)W_p(ldv(st + head));
+            if (state == S_WAITV) {
+                // after yielding: wait until the walker yielded to has moved on
+                if (vread(&ver[wait_on]) == wait_ver && vread(&prio[wait_on]) != INF) {
+                    if (waited_out()) break;
+                } else {
+                    state = S_IDLE;
+                    polls = 0;
+                }
+                continue;
+            }
+            if (state == S_WAITK) {
+                // asked walker wait_on to yield the head's successor hp: wait
+                // until that vertex has left its path (it is freed first)
+                const int32_t xw = head < 0 ? start : hp;
+                if (W_own(ldv(st + xw)) == (uint32_t)wait_on && vread(&prio[wait_on]) == wait_prio &&
+                    vread(&kill[me]) != myprio) {
+                    if (waited_out()) break;
+                } else {
+                    state = S_WALK;
+                    polls = 0;
+                }
+                continue;
+            }
+            if (state == S_POP) {
+                // one vertex of the loop popx -> ... -> head
+                const uint64_t wy = ldv(st + cur);
+                const int32_t nx = (int32_t)W_p(wy);
+                const uint32_t k = W_k(wy) + 1u;
+                if (k > K_MAX) { atomicOr(&sh_err, WERR_KOVF); break; }
+                if (W_own(wy) != me || ++walked > n) { atomicOr(&sh_err, WERR_LOOP); break; }
+                ++pops;
+                if (cur == popx) kx = k;
+                else stv(st + cur, W_pack(P_INVALID, k, OWN_FREE));
+                if (cur == head) {
+                    const int32_t px = succ<OFF64, WT>(g, popx, kx, tree, 0u, k0, k1);
+                    stv(st + popx, W_pack((uint32_t)px, kx, me));
+                    head = popx; hp = px;
+                    bump();
+                    state = S_WALK;
+                } else {
+                    cur = nx;
+                }
+                continue;
+            }
+            if (state == S_REL || state == S_SET) {
+                // one vertex of the path.  SET: start -> head.  REL: when a
+                // walker asked for vertex `cut`, first cut -> head, then
+                // start -> the vertex before cut; otherwise start -> head.
+                const uint64_t wy = ldv(st + cur);
+                if (W_own(wy) != me || ++walked > n) { atomicOr(&sh_err, WERR_LOOP); break; }
+                stv(st + cur, (wy & ~OWN_MASK) | (state == S_REL ? OWN_FREE : OWN_SET));
+                const int32_t nxt = (int32_t)W_p(wy);
+                bool last = false;
+                if (state == S_REL && cut >= 0) {
+                    if (cur == head) {           // end of the suffix pass
+                        if (start == cut) last = true;
+                        else { cur = start; head = -2; }   // head = -2 marks the prefix pass
+                    } else if (head == -2 && nxt == cut) {
+                        last = true;             // vertex before cut: prefix done
+                    } else {
+                        cur = nxt;
+                    }
+                } else if (cur == head) {
+                    last = true;
+                } else {
+                    cur = nxt;
+                }
+                if (!last) continue;
+                cut = -1;
+                if (state == S_REL) {
+                    drop_start(true);
+                    state = wait_on >= 0 ? S_WAITV : S_IDLE;
+                } else {
+                    drop_start(false);
+                    state = S_IDLE;
+                }
+                continue;
+            }
+            // S_WALK: one step of the loop-erased walk
+            if (vread(&kill[me]) == myprio) {
+                const int kb = vread(&killer[me]);
+                const int kv = vread(&killv[me]);
+                *(volatile int *)&kill[me] = -1;
+                wait_on = kb;
+                if (kb >= 0) wait_ver = vread(&ver[kb]);
+                cut = -1;
+                if (head >= 0 && kv >= 0 && kv < n && W_own(ldv(st + kv)) == me) {
+                    // free the requested vertex first
+                    cut = kv; cur = kv; walked = 0; state = S_REL;
+                } else if (head >= 0) { cur = start; walked = 0; state = S_REL; }
+                else { drop_start(true); state = wait_on >= 0 ? S_WAITV : S_IDLE; }
+                continue;
+            }
+            const int32_t x = head < 0 ? start : hp;
             const uint64_t wx = ldv(st + x);
             const uint32_t ox = W_own(wx);
             ++steps;
             if (ox == OWN_SET) {
-                if (head >= 0 && !path_set_owner(st, start, head, me, OWN_SET, n)) { atomicOr(&sh_err, WERR_LOOP); break; }
-                *(volatile int *)&prio[me] = 0x7fffffff;
-                bump();
-                start = -1; head = -1;
-                atomicSub(&sh_active, 1);
-                waited = 0;
+                if (head >= 0) { cur = start; walked = 0; state = S_SET; }
+                else { drop_start(false); state = S_IDLE; }
                 continue;
             }
             if (ox == me) {
-                // loop x -> ... -> head -> x: pop it
-                int32_t y = x;
-                bool ok = false;
-                uint32_t kx = 0;
-                for (int64_t q = 0; q <= n; ++q) {
-                    const uint64_t wy = ldv(st + y);
-                    const int32_t nx = (int32_t)W_p(wy);
-                    const uint32_t k = W_k(wy) + 1u;
-                    if (k > K_MAX) { atomicOr(&sh_err, WERR_KOVF); break; }
-                    ++pops;
-                    if (y == x) kx = k;
-                    else stv(st + y, W_pack(P_INVALID, k, OWN_FREE));
-                    if (y == head) { ok = true; break; }
-                    y = nx;
-                }
-                if (!ok) { atomicOr(&sh_err, WERR_LOOP); break; }
-                const int32_t px = succ<OFF64, WT>(g, x, kx, tree, 0u, k0, k1);
-                stv(st + x, W_pack((uint32_t)px, kx, me));
-                head = x;
-                bump();
+                cur = x; popx = x; walked = 0;
+                state = S_POP;
                 continue;
             }
             if (ox == OWN_FREE) {
+                // the successor draw does not depend on the claim: its loads are
+                // issued before the CAS result is used, so the two overlap
+                const bool draw = W_p(wx) == P_INVALID;
+                const int32_t px = draw ? succ<OFF64, WT>(g, x, W_k(wx), tree, 0u, k0, k1)
+                                        : (int32_t)W_p(wx);
                 const uint64_t claimed = (wx & ~OWN_MASK) | me;
-                if (atomicCAS((unsigned long long *)(st + x), (unsigned long long)wx,
-                              (unsigned long long)claimed) != wx)
-                    continue;
-                if (W_p(wx) == P_INVALID) {
-                    const int32_t px = succ<OFF64, WT>(g, x, W_k(wx), tree, 0u, k0, k1);
-                    stv(st + x, W_pack((uint32_t)px, W_k(wx), me));
-                }
+                if (cas_cta(st + x, wx, claimed) != wx) continue;
+                hp = px;
+                if (draw) stv(st + x, W_pack((uint32_t)hp, W_k(wx), me));
                 head = x;
                 bump();
-                waited = 0;
-                backoff = 32;
                 continue;
             }
-            // x belongs to another walker's path
-            const int op = *(volatile int *)&prio[ox];
+            // x is on another walker's path: the later walk yields
+            const int op = vread(&prio[ox]);
+            if (op == INF) continue;   // the owner has just dropped its walk: look again
             if (myprio < op) {
                 *(volatile int *)&killer[ox] = (int)me;
+                *(volatile int *)&killv[ox] = x;
                 __threadfence_block();
-                *(volatile int *)&kill[ox] = op;   // the later walk yields
-                if (++waited > max_wait) { atomicOr(&sh_err, WERR_WAIT); break; }
-                __nanosleep(backoff);
-                backoff = min(backoff * 2u, 1024u);
+                *(volatile int *)&kill[ox] = op;
+                wait_on = (int)ox; wait_prio = op; polls = 0;
+                state = S_WAITK;
             } else {
-                if (head >= 0 && !path_set_owner(st, start, head, me, OWN_FREE, n)) { atomicOr(&sh_err, WERR_LOOP); break; }
                 wait_on = (int)ox;
-                wait_ver = *(volatile int *)&ver[ox];
-                rq_push(rq, &sh_rtail, nstart, myprio);
-                ++yields;
-                *(volatile int *)&prio[me] = 0x7fffffff;
-                bump();
-                start = -1; head = -1;
-                atomicSub(&sh_active, 1);
+                wait_ver = vread(&ver[ox]);
+                cut = -1;
+                if (head >= 0) { cur = start; walked = 0; state = S_REL; }
+                else { drop_start(true); state = S_WAITV; }
             }
+            } while (0);
         }
         __syncthreads();
         if (threadIdx.x == 0 && sh_err) atomicOr(s.err, sh_err);
@@ -289,6 +395,9 @@ __global__ void __launch_bounds__(1024) w_trees(DevGraph g, WState s, int64_t B,
     if (steps) atomicAdd(&s.ctr[0], steps);
     if (yields) atomicAdd(&s.ctr[1], yields);
     if (pops) atomicAdd(&s.ctr[2], pops);
+    if (s.diag)
+        for (int i = 0; i < 8; ++i)
+            if (it_state[i]) atomicAdd(&s.diag[i], it_state[i]);
 }
 
 // visits_u = k_u + 1 over the chunk's trees into sums; optional per-tree output.
@@ -355,9 +464,6 @@ rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, 
     if (n >= ((int64_t)1 << 31) - 2) return set_error(RWC_ERR_UNSUPPORTED, "n too large for walker mode");
     const int32_t *order = nullptr;
     RWC_TRY(walker_order(G, &order));
-    int W = o.block_threads > 0 ? o.block_threads : (g.nnz / std::max<int64_t>(1, n) <= 6 ? 64 : 256);
-    W = std::max(32, std::min(1024, W / 32 * 32));
-    if (W > (int)OWN_SET) W = 1024;
     const size_t per_tree = (size_t)n * (8 + 4) + 256;
     int64_t B = o.trees_per_chunk;
     if (B <= 0) {
@@ -367,6 +473,15 @@ rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, 
         B = (int64_t)std::max<size_t>(1, budget / per_tree);
     }
     B = std::min(B, T);
+    // walkers per tree: fill the GPU's resident threads with the chunk's trees
+    int W = o.block_threads;
+    if (W <= 0) {
+        const int64_t threads = (int64_t)num_sms() * 2048;
+        const int64_t want = threads / std::max<int64_t>(1, B);
+        W = 64;
+        while (W < 1024 && 2 * W <= want) W *= 2;
+    }
+    W = std::max(32, std::min(1024, W / 32 * 32));
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     void *buf = nullptr;
     const size_t bytes = (size_t)B * n * 8 + (size_t)B * (n - 1) * 4 + 256;
@@ -384,6 +499,7 @@ rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, 
     ws.err = (int *)tail;                                  // @0
     ws.ctr = (unsigned long long *)(tail + 8);             // @8..40
     unsigned long long *draws = (unsigned long long *)(tail + 40);
+    ws.diag = (unsigned long long *)(tail + 64);
     const bool prof = o.profile != 0;
     cudaEvent_t ev[6] = {};
     if (prof) for (auto &e : ev) cudaEventCreate(&e);
@@ -391,12 +507,12 @@ rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, 
         cudaEvent_t *e; bool on;
         ~EvFree() { if (on) for (int i = 0; i < 6; ++i) cudaEventDestroy(e[i]); }
     } evf{ev, prof};
-    const int64_t max_wait = (int64_t)1 << 26;   // ~ tens of seconds of backoff
+    const int64_t max_wait = (int64_t)30 * 1000000000;   // 30 s per wait (ns)
     const int sms = num_sms();
     int64_t *h = G->host_scalars;
     for (int64_t c0 = 0; c0 < T; c0 += B) {
         const int64_t Bc = std::min(B, T - c0);
-        RWC_CUDA_TRY(cudaMemsetAsync(tail, 0, 64, stream));
+        RWC_CUDA_TRY(cudaMemsetAsync(tail, 0, 128, stream));
         RWC_CUDA_TRY(cudaMemsetAsync(ws.retry, 0, (size_t)Bc * (n - 1) * 4, stream));
         if (prof) cudaEventRecord(ev[0], stream);
         ::rwc::count_launches(1);
@@ -405,7 +521,7 @@ rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, 
         rwc_status status = RWC_OK;
         dispatch(g, [&](auto off64, auto wt) {
             auto kern = w_trees<decltype(off64)::value, decltype(wt)::value>;
-            const size_t smem = 4 * (size_t)W * sizeof(int);
+            const size_t smem = 5 * (size_t)W * sizeof(int);
             int per_sm = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W, smem);
             if (per_sm < 1) { status = set_error(RWC_ERR_UNSUPPORTED, "walker block does not fit"); return; }
@@ -421,12 +537,14 @@ rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, 
                                              visits ? visits + c0 * n : nullptr, draws);
         if (prof) cudaEventRecord(ev[3], stream);
         RWC_CUDA_TRY(cudaGetLastError());
-        RWC_CUDA_TRY(cudaMemcpyAsync(h, tail, 48, cudaMemcpyDeviceToHost, stream));
+        RWC_CUDA_TRY(cudaMemcpyAsync(h, tail, 128, cudaMemcpyDeviceToHost, stream));
         RWC_CUDA_TRY(cudaStreamSynchronize(stream));
         const int e = (int)(h[0] & 0xffffffff);
         if (e & WERR_KOVF) return set_error(RWC_ERR_UNSUPPORTED, "a vertex was popped more than 2^20 - 1 times");
         if (e & WERR_LOOP) return set_error(RWC_ERR_CUDA, "walker internal check failed");
         if (e & WERR_WAIT) return set_error(RWC_ERR_NOT_CONVERGED, "a walker wait exceeded its bound");
+        if (st)
+            for (int i = 0; i < 8; ++i) st->diag[i] += h[8 + i];
         if (st) {
             st->chunks += 1;
             st->walk_steps += h[1];
