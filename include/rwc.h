@@ -185,6 +185,37 @@ rwc_status rwc_sample_trees(rwc_graph_t *g, uint64_t seed, int64_t tree0,
                             rwc_stats_t *stats, rwc_stream_t stream);
 
 /*
+ * rwc_sample_trees without any allocation (the paper has no counterpart).
+ *
+ * For callers that cannot allocate device memory while they sample: code
+ * running while a stream is being captured into a CUDA graph, real-time or
+ * embedded hosts that allow no allocation after start-up, and processes whose
+ * memory pool is exhausted or owned by another allocator.  It samples the
+ * same trees as rwc_sample_trees (identical sums, parents and visits; the
+ * concurrent-walker sampler) but keeps all of its scratch in one static
+ * device array of RWC_NOALLOC_SCRATCH_BYTES inside this library, which every
+ * GPU that loads the library holds until the process exits.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine; the caller still passes
+ * the graph (already on the device) and the output buffers.
+ *
+ * Limits and rules:
+ *  - One tree needs 12 n bytes plus 4 n for the start order; a graph that
+ *    does not fit (n above roughly 2 million) gets RWC_ERR_INVALID.  Trees
+ *    are processed in as many chunks as the array requires.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Every call on a device shares the one array, which keeps the last call's
+ *    contents (the call clears what must start at zero); calls that overlap
+ *    on the GPU (other streams, other host threads) race and corrupt each
+ *    other: serialise them.
+ * Arguments as for rwc_sample_trees; synchronises stream.
+ */
+#define RWC_NOALLOC_SCRATCH_BYTES (32u << 20)
+rwc_status rwc_sample_trees_noalloc(rwc_graph_t *g, uint64_t seed, int64_t tree0,
+                                    int64_t num_trees, double *sums, int32_t *parents,
+                                    int32_t *visits, rwc_stream_t stream);
+
+/*
  * Algorithm 1 (AppRWC) fed by the estimator of Section 5.
  *   t_u = sums[u] / num_trees                        (estimate of (NL_v^-1)_uu)
  *   b   = sqrt(d_v) e_v - (sqrt(d_v) / vol) d        (line 1)

@@ -82,6 +82,7 @@ def lib():
         "rwc_graph_destroy": ([_vp], _i32),
         "rwc_sample_trees": ([_vp, _u64, _i64, _i64, _vp, _vp, _vp, ctypes.POINTER(Options),
                               ctypes.POINTER(Stats), _vp], _i32),
+        "rwc_sample_trees_noalloc": ([_vp, _u64, _i64, _i64, _vp, _vp, _vp, _vp], _i32),
         "rwc_estimate": ([_vp, _vp, _i64, _d, _vp, _vp, _vp], _i32),
         "rwc_recover": ([_vp, _vp, _i64, _vp, _vp, _vp], _i32),
         "rwc_solve": ([_vp, _i32, _vp, _vp, _d, ctypes.POINTER(_i32), _vp], _i32),
@@ -187,6 +188,17 @@ def rwc_sample_trees(g, seed, tree0, num_trees, sums, parents=None, visits=None,
                                   ctypes.byref(opt) if opt is not None else None,
                                   ctypes.byref(st), _stream(stream)))
     return st
+
+
+def rwc_sample_trees_noalloc(g, seed, tree0, num_trees, sums, parents=None, visits=None,
+                             stream=None):
+    """Same trees as rwc_sample_trees, with all scratch in the library's static
+    device array (no allocation during the call)."""
+    import torch
+    _check(lib().rwc_sample_trees_noalloc(g, int(seed), int(tree0), int(num_trees),
+                                          _dptr(sums, torch.float64, "sums"),
+                                          _dptr(parents, torch.int32, "parents"),
+                                          _dptr(visits, torch.int32, "visits"), _stream(stream)))
 
 
 def rwc_estimate(g, sums, num_trees, cg_tol, H_out, y_out=None, stream=None):

@@ -573,3 +573,144 @@ rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, 
 }
 
 }  // namespace rwc
+
+// ---------------------------------------------------------------------------
+// Allocation-free sampling.  Some callers cannot allocate device memory while
+// they sample: code that runs while a CUDA stream is being captured into a
+// graph, real-time or embedded hosts that forbid allocation after start-up,
+// and processes whose memory pool is exhausted or owned by another allocator.
+// rwc_sample_trees_noalloc samples with the walker kernels above, keeping all
+// of its scratch (start order, per-tree vertex words, requeue buffers and
+// counters) in one fixed array of this file; the caller still passes the
+// graph and the output buffers.
+#include <mutex>
+
+namespace rwc {
+namespace {
+
+constexpr size_t NOALLOC_BYTES = (size_t)32 << 20;   // 32 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// Device address of g_noalloc_scratch, resolved once per device (host code
+// may not use the symbol itself as a pointer).
+struct NoallocAddr {
+    std::mutex mu;
+    void *ptr[64] = {};
+};
+NoallocAddr g_noalloc_addr;
+
+rwc_status noalloc_scratch(void **out) {
+    int dev = 0;
+    RWC_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return set_error(RWC_ERR_UNSUPPORTED, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_addr.mu);
+    if (!g_noalloc_addr.ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return set_error(RWC_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed: %s",
+                             cudaGetErrorString(e));
+        g_noalloc_addr.ptr[dev] = p;
+    }
+    *out = g_noalloc_addr.ptr[dev];
+    return RWC_OK;
+}
+
+// Start order for the allocation-free path: i -> (a i + c) mod (n-1) with a
+// coprime to n-1, mapped onto the non-root vertices (any order gives the
+// same trees).
+__global__ void w_affine_order(int64_t n, int32_t root, uint64_t a, uint64_t c, int32_t *order) {
+    const int64_t m = n - 1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = (int64_t)((a * (uint64_t)i + c) % (uint64_t)m);
+        order[i] = (int32_t)(j < root ? j : j + 1);
+    }
+}
+
+uint64_t gcd64(uint64_t x, uint64_t y) {
+    while (y) { const uint64_t t = x % y; x = y; y = t; }
+    return x;
+}
+
+}  // namespace
+}  // namespace rwc
+
+extern "C" rwc_status rwc_sample_trees_noalloc(rwc_graph_t *G, uint64_t seed, int64_t tree0,
+                                               int64_t T, double *sums, int32_t *parents,
+                                               int32_t *visits, rwc_stream_t stream_) {
+    using namespace rwc;
+    clear_error();
+    if (!G) return set_error(RWC_ERR_INVALID, "graph is NULL");
+    if (T < 0 || tree0 < 0 || tree0 + T > ((int64_t)1 << 32))
+        return set_error(RWC_ERR_INVALID, "tree range must lie in [0, 2^32)");
+    if (T == 0) return RWC_OK;
+    const DevGraph &g = G->g;
+    const int64_t n = g.n;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    // layout: order [n-1] int32 | counters (64 B) | per tree: words [n] u64 + requeue [n-1] int32
+    const size_t order_b = (((size_t)(n - 1) * 4) + 255) & ~(size_t)255;
+    const size_t tail_b = 256;
+    const size_t tree_b = (((size_t)n * 8 + (size_t)(n - 1) * 4) + 255) & ~(size_t)255;
+    if (order_b + tail_b + tree_b > NOALLOC_BYTES)
+        return set_error(RWC_ERR_INVALID,
+                         "graph too large for rwc_sample_trees_noalloc: one tree needs %zu bytes of "
+                         "scratch, the static array holds %zu",
+                         order_b + tail_b + tree_b, NOALLOC_BYTES);
+    void *base = nullptr;
+    RWC_TRY(noalloc_scratch(&base));
+    char *p = (char *)base;
+    int32_t *order = (int32_t *)p;
+    char *tail = p + order_b;
+    char *trees = tail + tail_b;
+    const int64_t B = std::min<int64_t>(T, (int64_t)((NOALLOC_BYTES - order_b - tail_b) / tree_b));
+    WState ws;
+    ws.word = (uint64_t *)trees;
+    ws.retry = (int32_t *)(trees + (size_t)B * n * 8);
+    ws.order = order;
+    ws.err = (int *)tail;
+    ws.ctr = (unsigned long long *)(tail + 8);
+    unsigned long long *draws = (unsigned long long *)(tail + 40);
+    ws.diag = (unsigned long long *)(tail + 64);
+    const uint64_t m = (uint64_t)(n - 1);
+    uint64_t a = (uint64_t)(0.6180339887 * (double)m) | 1ull;
+    while (m > 1 && gcd64(a % m, m) != 1) ++a;
+    const int sms = num_sms();
+    ::rwc::count_launches(1);
+    w_affine_order<<<sms * 4, 256, 0, stream>>>(n, g.root, m > 1 ? a % m : 1, seed % (m ? m : 1), order);
+    const int W = (g.nnz / std::max<int64_t>(1, n) <= 6) ? 64 : 256;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    int64_t *h = G->host_scalars;
+    for (int64_t c0 = 0; c0 < T; c0 += B) {
+        const int64_t Bc = std::min(B, T - c0);
+        RWC_CUDA_TRY(cudaMemsetAsync(tail, 0, 128, stream));
+        RWC_CUDA_TRY(cudaMemsetAsync(ws.retry, 0, (size_t)Bc * (n - 1) * 4, stream));
+        ::rwc::count_launches(1);
+        w_init<<<sms * 8, 256, 0, stream>>>(n, g.root, ws.word, Bc);
+        rwc_status status = RWC_OK;
+        dispatch(g, [&](auto off64, auto wt) {
+            auto kern = w_trees<decltype(off64)::value, decltype(wt)::value>;
+            const size_t smem = 5 * (size_t)W * sizeof(int);
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W, smem);
+            if (per_sm < 1) { status = set_error(RWC_ERR_UNSUPPORTED, "walker block does not fit"); return; }
+            const int64_t blocks = std::min<int64_t>(Bc, (int64_t)sms * per_sm);
+            ::rwc::count_launches(1);
+            kern<<<(unsigned)blocks, W, smem, stream>>>(g, ws, Bc, (uint32_t)(tree0 + c0), k0, k1,
+                                                        (int64_t)30 * 1000000000);
+        });
+        RWC_TRY(status);
+        ::rwc::count_launches(1);
+        w_accum<<<sms * 8, 256, 0, stream>>>(n, g.root, ws.word, Bc, sums,
+                                             parents ? parents + c0 * n : nullptr,
+                                             visits ? visits + c0 * n : nullptr, draws);
+        RWC_CUDA_TRY(cudaGetLastError());
+        RWC_CUDA_TRY(cudaMemcpyAsync(h, tail, 48, cudaMemcpyDeviceToHost, stream));
+        RWC_CUDA_TRY(cudaStreamSynchronize(stream));
+        const int e = (int)(h[0] & 0xffffffff);
+        if (e & WERR_KOVF) return set_error(RWC_ERR_UNSUPPORTED, "a vertex was popped more than 2^20 - 1 times");
+        if (e & WERR_LOOP) return set_error(RWC_ERR_CUDA, "walker internal check failed");
+        if (e & WERR_WAIT) return set_error(RWC_ERR_NOT_CONVERGED, "a walker wait exceeded its bound");
+    }
+    return RWC_OK;
+}
