@@ -40,6 +40,7 @@ WORKLOADS = {
     "ba2000": [("ba2000", 1000)],
     "grid512": [("grid512", 64)],
     "rmat18": [("rmat18", 512)],
+    "batch4096": [("batch4096", 256)],
     "rmat24": [("rmat24", 500)],
 }
 
@@ -191,6 +192,49 @@ def run_reference(args, rank):
 METRIC = "spanning trees/s and RWC nodes/s at <=1% mean rel err; % of HBM roofline"
 
 
+def run_batch(args, rwc, torch, dev, world, rank):
+    """4096 small graphs (sizes log-uniform in [50, 20000], ER / BA / RGG),
+    256 trees each: one persistent launch per size class, replayed from a CUDA
+    graph, against one launch per graph."""
+    import synth
+    T = WORKLOADS["batch4096"][0][1]
+    specs = synth.batch_specs(4096, seed=0)
+    gs = [synth.batch_graph(i, n, kind, seed=0) for i, (n, kind) in enumerate(specs)]
+    B = rwc.Batch(gs)
+    B.autotune(None)
+    sums = torch.zeros(B.N, dtype=torch.float64, device=dev)
+    res = {}
+    for name, kw in (("persistent_graph", dict(use_graph=1)), ("per_graph_launch", dict(per_graph_launch=1))):
+        for _ in range(args.warmup):
+            sums.zero_()
+            B.sample(T, seed=1, sums=sums, **kw)
+        torch.cuda.synchronize()
+        t = []
+        draws = 0
+        for _ in range(args.steps):
+            sums.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, st = B.sample(T, seed=1, sums=sums, **kw)
+            e1.record()
+            torch.cuda.synchronize()
+            t.append(e0.elapsed_time(e1))
+            draws = st.draws
+        ms = float(np.mean(t))
+        res[name] = {"ms_per_step": ms, "trees_per_s": world * 4096 * T / (ms / 1000.0),
+                     "nodes_per_s": world * B.N / (ms / 1000.0), "draws_per_step": int(draws)}
+    if rank == 0:
+        line = {"metric": METRIC, "value": res["persistent_graph"]["trees_per_s"], "unit": "trees/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": res["persistent_graph"]["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
+                "config": {"workload": "batch4096", "graphs": 4096, "total_vertices": int(B.N),
+                           "trees_per_graph": T},
+                "batch": res,
+                "speedup_vs_per_graph_launch": res["per_graph_launch"]["ms_per_step"] / res["persistent_graph"]["ms_per_step"]}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -203,6 +247,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=20.0)
     ap.add_argument("--walkers", type=int, default=0, help="walkers per tree (0 = auto)")
+    ap.add_argument("--policy", type=int, default=0, help="walker conflict policy (0 auto, 1 yield, 2 wait)")
     args = ap.parse_args()
     if args.trees:
         WORKLOADS[args.workload] = [(k, args.trees) for k, _ in WORKLOADS[args.workload]]
@@ -226,6 +271,13 @@ def main():
     dev = torch.device("cuda", local)
     hbm_peak, peak_src = load_peaks()
 
+    if args.workload == "batch4096":
+        run_batch(args, rwc, torch, dev, world, rank)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
     graphs = []
     for key, T in WORKLOADS[args.workload]:
         g = make_graph(key)
@@ -233,7 +285,7 @@ def main():
         sums = torch.zeros(g.n, dtype=torch.float64, device=dev)
         graphs.append((key, T, g, G, sums))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    opt = rwc.Options(profile=1, block_threads=args.walkers)
+    opt = rwc.Options(profile=1, block_threads=args.walkers, walker_policy=args.policy)
     tree_base = rank * 10_000_000
 
     def step(stats_out=None):

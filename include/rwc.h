@@ -80,11 +80,17 @@ typedef struct {
     int64_t trees_per_chunk;  /* GLOBAL/WALKER: trees resident at once (0 = auto) */
     int32_t use_jumps;        /* GLOBAL mode: 1 = jump pointers (default), 0 = off,
                                  -1 = default */
-    int32_t block_threads;    /* SHARED: block size; WALKER: walkers per tree (0 = auto) */
+    int32_t block_threads;    /* SHARED: block size; WALKER: walkers per tree, at most
+                                 512 (0 = auto) */
     int64_t memory_budget;    /* GLOBAL/WALKER: bytes of scratch to use (0 = auto) */
     int32_t profile;          /* 1 = time every kernel launch with CUDA events on
-                                 the call's stream (fills rwc_stats_t.phase_*) */
-    int32_t reserved;
+                                 the call's stream (fills rwc_stats_t.phase_*);
+                                 2 = also count walker loop iterations per state
+                                 (rwc_stats_t.diag; slower kernel variant) */
+    int32_t walker_policy;    /* WALKER mode, when a walk runs into an earlier
+                                 walk's path: 0 = default (1), 1 = yield (free the
+                                 path, requeue), 2 = wait (keep the path until the
+                                 vertex changes owner) */
 } rwc_options_t;
 
 /* Sampler phases reported in rwc_stats_t.  GLOBAL mode: INIT, WALK, POP
@@ -116,7 +122,7 @@ typedef struct {
     int64_t phase_units[RWC_NPHASE];
     /* diagnostics; WALKER mode: loop iterations summed over all walkers in
      * the states idle, walk, pop, release, settle, wait-for-yield,
-     * wait-after-yield */
+     * wait-after-yield (or wait for an earlier walk's vertex) */
     int64_t diag[8];
 } rwc_stats_t;
 

@@ -12,7 +12,11 @@
 #include <cstring>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "rwc_common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace rwc {
 namespace {
@@ -315,6 +319,81 @@ __global__ void inner_update(int64_t n, int k, const double *rz, const double *p
     }
 }
 
+// One-launch inner PCG for a single right-hand side (cooperative launch,
+// grid-wide synchronisation between the phases of an iteration).  Scalars of
+// iteration it live at sc[3 it + {0: <p,q>, 1: <r,z>, 2: <r,r>}]; every block
+// reads the same reduced values after a grid sync, so the loop exit (relative
+// residual at most tol, or no halving of <r,r> for `window` iterations, or
+// max_it) is taken by all blocks together.  out[0] = iterations, out[1] = last <r,r>.
+template <int VW, bool OFF64, bool W>
+__global__ void __launch_bounds__(TPB) cg1_coop(DevGraph g, const float *__restrict__ dinv,
+                                                float *r, float *e, float *z, float *p, float *q,
+                                                double *sc, int max_it, double tol2, int window,
+                                                double *out) {
+    cg::grid_group grid = cg::this_grid();
+    const int sub = threadIdx.x & (VW - 1);
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+    const int64_t row0 = tid / VW, nrows = nthr / VW;
+    double best = INFINITY, rr = sc[2] > 0 ? sc[2] : 1.0;
+    int since = 0, it = 0;
+    for (; it < max_it; ++it) {
+        double *cur = sc + 3 * (size_t)it, *nxt = cur + 3;
+        // q = L p and <p, q>
+        double acc = 0.0;
+        for (int64_t u0 = row0 - (row0 % (32 / VW)); u0 < g.n; u0 += nrows) {
+            const int64_t u = u0 + (row0 % (32 / VW));
+            float sacc = 0.f;
+            if (u < g.n) {
+                int64_t b, e2;
+                rowb<OFF64>(g, u, b, e2);
+                for (int64_t j = b + sub; j < e2; j += VW) sacc += (W ? g.w[j] : 1.f) * p[g.col[j]];
+            }
+#pragma unroll
+            for (int o = VW / 2; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o, VW);
+            if (sub == 0 && u < g.n) {
+                const float pu = p[u];
+                const float qu = (float)g.d[u] * pu - sacc;
+                q[u] = qu;
+                acc += (double)pu * (double)qu;
+            }
+        }
+        acc = warp_sum(acc);
+        if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(&cur[0], acc);
+        grid.sync();
+        // step and the new residual
+        const double den = *(volatile double *)&cur[0], rz = *(volatile double *)&cur[1];
+        const float a = (den > 0.0 && rz > 0.0) ? (float)(rz / den) : 0.f;
+        double a1 = 0.0, a2 = 0.0;
+        for (int64_t i = tid; i < g.n; i += nthr) {
+            e[i] += a * p[i];
+            const float rv = r[i] - a * q[i];
+            r[i] = rv;
+            const float zv = dinv[i] * rv;
+            z[i] = zv;
+            a1 += (double)rv * (double)zv;
+            a2 += (double)rv * (double)rv;
+        }
+        a1 = warp_sum(a1);
+        a2 = warp_sum(a2);
+        if ((threadIdx.x & 31) == 0) {
+            if (a1 != 0.0) atomicAdd(&nxt[1], a1);
+            if (a2 != 0.0) atomicAdd(&nxt[2], a2);
+        }
+        grid.sync();
+        rr = *(volatile double *)&nxt[2];
+        const double rz1 = *(volatile double *)&nxt[1];
+        if (!(rr == rr) || rr <= tol2) { ++it; break; }
+        if (rr < 0.25 * best) { best = rr; since = 0; }
+        else if (++since >= window) { ++it; break; }
+        // new direction
+        const float bta = rz > 0.0 ? (float)(rz1 / rz) : 0.f;
+        for (int64_t i = tid; i < g.n; i += nthr) p[i] = z[i] + bta * p[i];
+        grid.sync();
+    }
+    if (tid == 0) { out[0] = (double)it; out[1] = rr; }
+}
+
 // p = z + beta p, beta_c = rz1[c] / rz0[c].
 __global__ void inner_dir(int64_t n, int k, const double *rz0, const double *rz1, const float *z,
                           float *p) {
@@ -402,6 +481,10 @@ rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, doub
     const unsigned gs = grid_for(nk), gw = grid_for(n * 32);
     const int vw = pick_vw(g);
     const unsigned gv = grid_for(n * vw);
+    int dev = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    const bool coop_ok = coop != 0;
 
     RWC_CUDA_TRY(cudaMemsetAsync(X, 0, (size_t)nk * sizeof(double), st));
     std::vector<double> h(3 * (size_t)k), bn(k);
@@ -442,6 +525,41 @@ rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, doub
         // inner FP32 PCG on the normalised residual
         RWC_CUDA_TRY(cudaMemsetAsync(it_sc, 0, sc_count * sizeof(double) - 8 * shk, st));
         ::rwc::count_launches(1); inner_start<<<gs, TPB, shk, st>>>(n, k, R, outer_sc + k, g.dinv32, r, e, z, p, it_sc + 1 * k);
+        if (k == 1 && coop_ok) {
+            // one cooperative launch for the whole inner solve
+            double *outv = outer_sc + 4;
+            int mi = max_inner;
+            double t2 = inner_tol * inner_tol;
+            int window = 1024;
+            bool launched = false;
+            dispatch(g, [&](auto o64, auto wt) {
+                dispatch_vw(vw, [&](auto V) {
+                    auto kern = cg1_coop<decltype(V)::value, decltype(o64)::value, decltype(wt)::value>;
+                    int per_sm = 0;
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TPB, 0);
+                    if (per_sm < 1) return;
+                    const unsigned blocks = (unsigned)std::min<int64_t>((int64_t)num_sms() * per_sm, gv);
+                    const float *dinv = g.dinv32;
+                    float *rr_ = r, *ee = e, *zz = z, *pp = p, *qq = Qv;
+                    double *scp = it_sc;
+                    DevGraph gg = g;
+                    void *args[] = {&gg, &dinv, &rr_, &ee, &zz, &pp, &qq, &scp, &mi, &t2, &window, &outv};
+                    ::rwc::count_launches(1);
+                    if (cudaLaunchCooperativeKernel((const void *)kern, blocks, TPB, args, 0, st) == cudaSuccess)
+                        launched = true;
+                });
+            });
+            if (launched) {
+                double hv[2];
+                RWC_CUDA_TRY(cudaMemcpyAsync(hv, outv, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+                RWC_CUDA_TRY(cudaStreamSynchronize(st));
+                total_iters += (int)hv[0];
+                ::rwc::count_launches(1); outer_add<<<gs, TPB, 0, st>>>(n, k, outer_sc + k, e, X);
+                RWC_CUDA_TRY(cudaGetLastError());
+                continue;
+            }
+            (void)cudaGetLastError();
+        }
         int it = 0;
         const int check = 16;
         bool inner_done = false;

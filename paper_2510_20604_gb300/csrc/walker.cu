@@ -128,11 +128,12 @@ __device__ __forceinline__ uint64_t gtimer() {
 // Walker states.  Each loop iteration does at most one vertex of work, so
 // the lanes of a warp stay close to each other in the loop; waits poll
 // shared memory only.
-enum : int { S_IDLE = 0, S_WALK, S_POP, S_REL, S_SET, S_WAITK, S_WAITV, S_DONE };
+enum : int { S_IDLE = 0, S_WALK, S_POP, S_REL, S_SET, S_WAITK, S_WAITV, S_WAITH, S_DONE };
 
-template <bool OFF64, bool WT>
-__global__ void __launch_bounds__(1024) w_trees(DevGraph g, WState s, int64_t B, uint32_t tree0,
-                                                uint32_t k0, uint32_t k1, int64_t max_wait_ns) {
+template <bool OFF64, bool WT, bool DIAG>
+__global__ void __launch_bounds__(512, 3) w_trees(DevGraph g, WState s, int64_t B, uint32_t tree0,
+                                                uint32_t k0, uint32_t k1, int64_t max_wait_ns,
+                                                int wait_policy) {
     const int64_t n = g.n;
     const int64_t nstart = n - 1;
     const uint32_t me = threadIdx.x;
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(1024) w_trees(DevGraph g, WState s, int64_t B,
     int *ver = sh + 3 * blockDim.x;
     int *killv = sh + 4 * blockDim.x;   // the contested vertex of a yield request
     unsigned long long steps = 0, yields = 0, pops = 0;
-    unsigned long long it_state[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned long long it_state[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 
     for (;;) {
         if (threadIdx.x == 0) {
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(1024) w_trees(DevGraph g, WState s, int64_t B,
             if (__any_sync(0xffffffffu, err)) break;
             if (__all_sync(0xffffffffu, state == S_DONE)) break;
             if (state == S_DONE) continue;
-            ++it_state[state];
+            if (DIAG) ++it_state[state];
             do {
             if (state == S_IDLE) {
                 // a fresh start, else a requeued one
@@ -254,6 +255,19 @@ __global__ void __launch_bounds__(1024) w_trees(DevGraph g, WState s, int64_t B,
                     if (waited_out()) break;
                 } else {
                     state = S_IDLE;
+                    polls = 0;
+                }
+                continue;
+            }
+            if (state == S_WAITH) {
+                // wait policy: the head's successor lies on an earlier walk's
+                // path; keep this path and wait until that vertex changes owner
+                // (a request to yield is served from here too)
+                const int32_t xw = head < 0 ? start : hp;
+                if (vread(&kill[me]) != myprio && W_own(ldv(st + xw)) == (uint32_t)wait_on) {
+                    if (waited_out()) break;
+                } else {
+                    state = S_WALK;
                     polls = 0;
                 }
                 continue;
@@ -379,6 +393,9 @@ __global__ void __launch_bounds__(1024) w_trees(DevGraph g, WState s, int64_t B,
                 *(volatile int *)&kill[ox] = op;
                 wait_on = (int)ox; wait_prio = op; polls = 0;
                 state = S_WAITK;
+            } else if (wait_policy) {
+                wait_on = (int)ox; polls = 0;
+                state = S_WAITH;
             } else {
                 wait_on = (int)ox;
                 wait_ver = vread(&ver[ox]);
@@ -395,9 +412,11 @@ __global__ void __launch_bounds__(1024) w_trees(DevGraph g, WState s, int64_t B,
     if (steps) atomicAdd(&s.ctr[0], steps);
     if (yields) atomicAdd(&s.ctr[1], yields);
     if (pops) atomicAdd(&s.ctr[2], pops);
-    if (s.diag)
-        for (int i = 0; i < 8; ++i)
-            if (it_state[i]) atomicAdd(&s.diag[i], it_state[i]);
+    if (DIAG && s.diag)
+        for (int i = 0; i < 8; ++i) {
+            const unsigned long long v = it_state[i] + (i == S_WAITV ? it_state[S_WAITH] : 0ull);
+            if (v) atomicAdd(&s.diag[i], v);
+        }
 }
 
 // visits_u = k_u + 1 over the chunk's trees into sums; optional per-tree output.
@@ -479,9 +498,9 @@ rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, 
         const int64_t threads = (int64_t)num_sms() * 2048;
         const int64_t want = threads / std::max<int64_t>(1, B);
         W = 64;
-        while (W < 1024 && 2 * W <= want) W *= 2;
+        while (W < 512 && 2 * W <= want) W *= 2;
     }
-    W = std::max(32, std::min(1024, W / 32 * 32));
+    W = std::max(32, std::min(512, W / 32 * 32));   // the kernel is built for <= 512 threads
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     void *buf = nullptr;
     const size_t bytes = (size_t)B * n * 8 + (size_t)B * (n - 1) * 4 + 256;
@@ -520,14 +539,16 @@ rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, 
         if (prof) cudaEventRecord(ev[1], stream);
         rwc_status status = RWC_OK;
         dispatch(g, [&](auto off64, auto wt) {
-            auto kern = w_trees<decltype(off64)::value, decltype(wt)::value>;
+            auto kern = (o.profile >= 2) ? w_trees<decltype(off64)::value, decltype(wt)::value, true>
+                                         : w_trees<decltype(off64)::value, decltype(wt)::value, false>;
             const size_t smem = 5 * (size_t)W * sizeof(int);
             int per_sm = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W, smem);
             if (per_sm < 1) { status = set_error(RWC_ERR_UNSUPPORTED, "walker block does not fit"); return; }
             const int64_t blocks = std::min<int64_t>(Bc, (int64_t)sms * per_sm);
             ::rwc::count_launches(1);
-            kern<<<(unsigned)blocks, W, smem, stream>>>(g, ws, Bc, (uint32_t)(tree0 + c0), k0, k1, max_wait);
+            kern<<<(unsigned)blocks, W, smem, stream>>>(g, ws, Bc, (uint32_t)(tree0 + c0), k0, k1, max_wait,
+                                                        o.walker_policy == 2 ? 1 : 0);
         });
         RWC_TRY(status);
         if (prof) cudaEventRecord(ev[2], stream);
@@ -689,7 +710,7 @@ extern "C" rwc_status rwc_sample_trees_noalloc(rwc_graph_t *G, uint64_t seed, in
         w_init<<<sms * 8, 256, 0, stream>>>(n, g.root, ws.word, Bc);
         rwc_status status = RWC_OK;
         dispatch(g, [&](auto off64, auto wt) {
-            auto kern = w_trees<decltype(off64)::value, decltype(wt)::value>;
+            auto kern = w_trees<decltype(off64)::value, decltype(wt)::value, false>;
             const size_t smem = 5 * (size_t)W * sizeof(int);
             int per_sm = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W, smem);
@@ -697,7 +718,7 @@ extern "C" rwc_status rwc_sample_trees_noalloc(rwc_graph_t *G, uint64_t seed, in
             const int64_t blocks = std::min<int64_t>(Bc, (int64_t)sms * per_sm);
             ::rwc::count_launches(1);
             kern<<<(unsigned)blocks, W, smem, stream>>>(g, ws, Bc, (uint32_t)(tree0 + c0), k0, k1,
-                                                        (int64_t)30 * 1000000000);
+                                                        (int64_t)30 * 1000000000, 1);
         });
         RWC_TRY(status);
         ::rwc::count_launches(1);

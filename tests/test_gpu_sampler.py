@@ -46,7 +46,9 @@ MODES = {"shared": rwc.Options(mode=rwc.MODE_SHARED),
          "global_chunk3": rwc.Options(mode=rwc.MODE_GLOBAL, trees_per_chunk=3),
          "walker": rwc.Options(mode=rwc.MODE_WALKER),
          "walker_w32_chunk5": rwc.Options(mode=rwc.MODE_WALKER, block_threads=32, trees_per_chunk=5),
-         "walker_w1024": rwc.Options(mode=rwc.MODE_WALKER, block_threads=1024)}
+         "walker_w1024": rwc.Options(mode=rwc.MODE_WALKER, block_threads=1024),
+         "walker_yield": rwc.Options(mode=rwc.MODE_WALKER, walker_policy=1),
+         "walker_yield_w32": rwc.Options(mode=rwc.MODE_WALKER, walker_policy=1, block_threads=32)}
 
 
 @pytest.mark.parametrize("mode", list(MODES))
@@ -66,12 +68,13 @@ def test_small_ba_config_bit_exact(mode):
     assert_exact(g, 1000, opt)
 
 
-@pytest.mark.parametrize("mode", ["global", "global_nojump", "walker", "walker_w64"])
+@pytest.mark.parametrize("mode", ["global", "global_nojump", "walker", "walker_w64", "walker_yield"])
 def test_grid_several_chunks_bit_exact(mode):
     g = synth.grid2d(61, 67)
     if mode.startswith("walker"):
         opt = rwc.Options(mode=rwc.MODE_WALKER, trees_per_chunk=9,
-                          block_threads=64 if mode == "walker_w64" else 0)
+                          block_threads=64 if mode == "walker_w64" else 0,
+                          walker_policy=1 if mode == "walker_yield" else 0)
     else:
         opt = rwc.Options(mode=rwc.MODE_GLOBAL, trees_per_chunk=9,
                           use_jumps=0 if mode == "global_nojump" else -1)
