@@ -64,6 +64,28 @@ def bytes_per_unit(phase, mode, weighted, off64):
             "finish": 9, "accum": 12}[phase]
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# dominant kernel, from one ncu capture per workload; valid only for the kernel
+# source it was measured on (SHA-256 of the .cu file), else reported as null.
+TRAFFIC = {
+    # (workload, kernel): (bytes per launch, source file, sha256 of the source)
+}
+
+
+def traffic_for(workload, kernel):
+    import hashlib
+    ent = TRAFFIC.get((workload, kernel))
+    if not ent:
+        return None
+    nbytes, src, sha = ent
+    path = os.path.join(ROOT, "paper_2510_20604_gb300", "csrc", src)
+    try:
+        cur = hashlib.sha256(open(path, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return nbytes if cur == sha else None
+
+
 def make_graph(key):
     import synth
     if key == "grid1024":
@@ -248,6 +270,7 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=20.0)
     ap.add_argument("--walkers", type=int, default=0, help="walkers per tree (0 = auto)")
     ap.add_argument("--policy", type=int, default=0, help="walker conflict policy (0 auto, 1 yield, 2 wait)")
+    ap.add_argument("--diag", action="store_true", help="count walker loop iterations per state (slower)")
     args = ap.parse_args()
     if args.trees:
         WORKLOADS[args.workload] = [(k, args.trees) for k, _ in WORKLOADS[args.workload]]
@@ -285,7 +308,7 @@ def main():
         sums = torch.zeros(g.n, dtype=torch.float64, device=dev)
         graphs.append((key, T, g, G, sums))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    opt = rwc.Options(profile=1, block_threads=args.walkers, walker_policy=args.policy)
+    opt = rwc.Options(profile=2 if args.diag else 1, block_threads=args.walkers, walker_policy=args.policy)
     tree_base = rank * 10_000_000
 
     def step(stats_out=None):
@@ -371,8 +394,10 @@ def main():
     per_launch_bytes = phase_bytes[dom] / nl
     per_launch_s = phase_ms[dom] / 1000.0 / nl
     achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
+    kname = KERNEL_NAMES.get(dom_mode, {}).get(dom, dom)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None,
+                "frac": achieved / hbm_peak, "traffic": traffic_for(args.workload, kname),
+                "algorithmic_bytes_per_launch": per_launch_bytes,
                 "kernel": KERNEL_NAMES.get(dom_mode, {}).get(dom, dom),
                 "unit_bytes": bytes_per_unit(dom, dom_mode, False, False),
                 "peak_source": f"{peak_src} hbm_gbs",
@@ -454,7 +479,8 @@ def main():
             "step_ms": step_ms,
             "sampler_stats": [{"graph": k, "mode": st["mode"], "rounds_or_yields": st["rounds"],
                                "draws": st["draws"], "walk_steps": st["walk_steps"],
-                               "chunks": st["chunks"], "diag": st["diag"]}
+                               "chunks": st["chunks"], "walkers_per_tree": st["block_threads"],
+                               "diag": st["diag"]}
                               for k, st in all_stats[-len(graphs):]],
         }
         print(json.dumps(line), flush=True)

@@ -89,8 +89,10 @@ typedef struct {
                                  (rwc_stats_t.diag; slower kernel variant) */
     int32_t walker_policy;    /* WALKER mode, when a walk runs into an earlier
                                  walk's path: 0 = default (1), 1 = yield (free the
-                                 path, requeue), 2 = wait (keep the path until the
-                                 vertex changes owner) */
+                                 path, requeue, wait for the earlier walk to move
+                                 on), 2 = wait (keep the path until the vertex
+                                 changes owner), 3 = yield and take a fresh start
+                                 at once while fresh starts remain */
 } rwc_options_t;
 
 /* Sampler phases reported in rwc_stats_t.  GLOBAL mode: INIT, WALK, POP
@@ -111,7 +113,7 @@ typedef struct {
     int64_t walk_steps;   /* GLOBAL: pointer-chasing steps; WALKER: walker steps */
     int64_t chunks;       /* tree chunks processed */
     int32_t mode;         /* mode actually used */
-    int32_t reserved;
+    int32_t block_threads; /* WALKER: walkers (threads) per tree of the last chunk */
     int64_t marked;       /* compressed-graph nodes over all rounds (= draws) */
     /* with rwc_options_t.profile: device time (ms), launches and work units
      * per phase; units are vertices (INIT, ACCUM), pointer-chasing steps (WALK

@@ -45,15 +45,13 @@ class Options(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("trees", ctypes.c_int64), ("draws", ctypes.c_int64), ("rounds", ctypes.c_int64),
                 ("walk_steps", ctypes.c_int64), ("chunks", ctypes.c_int64), ("mode", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("marked", ctypes.c_int64),
+                ("block_threads", ctypes.c_int32), ("marked", ctypes.c_int64),
                 ("phase_ms", ctypes.c_double * NPHASE), ("phase_launches", ctypes.c_int64 * NPHASE),
                 ("phase_units", ctypes.c_int64 * NPHASE), ("diag", ctypes.c_int64 * 8)]
 
     def as_dict(self):
         out = {}
         for f, _ in self._fields_:
-            if f == "reserved":
-                continue
             v = getattr(self, f)
             out[f] = list(v) if (f.startswith("phase_") or f == "diag") else v
         return out

@@ -95,21 +95,6 @@ __global__ void w_init(int64_t n, int32_t root, uint64_t *word, int64_t B) {
     }
 }
 
-// Walk a walker's path from s to h applying `own` to every vertex (FREE keeps
-// the cached successor, SET makes it final).  Returns false on a broken path.
-__device__ __forceinline__ bool path_set_owner(uint64_t *st, int32_t s, int32_t h, uint32_t me,
-                                               uint32_t own, int64_t n) {
-    int32_t y = s;
-    for (int64_t q = 0; q <= n; ++q) {
-        const uint64_t w = ldv(st + y);
-        if (W_own(w) != me) return false;
-        stv(st + y, (w & ~OWN_MASK) | own);
-        if (y == h) return true;
-        y = (int32_t)W_p(w);
-    }
-    return false;
-}
-
 // Retry queue: slots hold start index + 1 (0 = empty); a producer reserves a
 // slot with the tail counter and then fills it, a consumer reserves with the
 // head counter and waits (bounded) for the fill, then empties the slot.
@@ -125,13 +110,17 @@ __device__ __forceinline__ uint64_t gtimer() {
     return t;
 }
 
-// Walker states.  Each loop iteration does at most one vertex of work, so
-// the lanes of a warp stay close to each other in the loop; waits poll
-// shared memory only.
+// Walker states.  Each loop iteration ("tick") does at most one vertex of
+// work per walker, and the memory accesses of all states are issued by the
+// same instructions: one load of a vertex word (with the row bounds of the
+// vertex that may be drawn), then the stores, the claim CAS and the
+// successor draw, whose arc load overlaps the CAS.  The lanes of a warp thus
+// pay about two dependent memory round trips per tick, whatever mix of
+// states they are in.  Waits poll shared memory or the one vertex word.
 enum : int { S_IDLE = 0, S_WALK, S_POP, S_REL, S_SET, S_WAITK, S_WAITV, S_WAITH, S_DONE };
 
 template <bool OFF64, bool WT, bool DIAG>
-__global__ void __launch_bounds__(512, 3) w_trees(DevGraph g, WState s, int64_t B, uint32_t tree0,
+__global__ void __launch_bounds__(512, 2) w_trees(DevGraph g, WState s, int64_t B, uint32_t tree0,
                                                 uint32_t k0, uint32_t k1, int64_t max_wait_ns,
                                                 int wait_policy) {
     const int64_t n = g.n;
@@ -172,8 +161,10 @@ __global__ void __launch_bounds__(512, 3) w_trees(DevGraph g, WState s, int64_t 
         int state = S_IDLE;
         int32_t start = -1, head = -1, hp = -1, cur = -1, popx = -1;
         int32_t cut = -1;             // release: suffix from `cut` first, then the prefix
-        uint32_t kx = 0;
+        uint32_t kx = 0;              // new pop count of the vertex a pop re-enters
         int myprio = INF, wait_on = -1, wait_ver = 0, wait_prio = 0;
+        int pend_idx = -1;            // next fresh start, fetched one walk ahead
+        int32_t pend_start = -1;
         int64_t walked = 0;          // vertices visited in the current POP/REL/SET pass
         int64_t polls = 0;
         uint64_t wait_t0 = 0;
@@ -188,6 +179,19 @@ __global__ void __launch_bounds__(512, 3) w_trees(DevGraph g, WState s, int64_t 
             }
             return false;
         };
+        // after a yield: wait for the winner to move on before the next start
+        // (policy bit 2 skips the wait while fresh starts remain, since a
+        // fresh start is elsewhere in the graph)
+        auto must_wait = [&]() {
+            return !(wait_policy & 2) || (pend_idx < 0 && vread(&sh_next) >= nstart);
+        };
+        auto take_fresh = [&]() {
+            if (vread(&sh_next) < nstart) {
+                const int i = atomicAdd(&sh_next, 1);
+                if (i < nstart) return i;
+            }
+            return -1;
+        };
         auto drop_start = [&](bool requeue) {
             if (requeue) {
                 rq_push(rq, &sh_rtail, nstart, myprio);
@@ -199,11 +203,10 @@ __global__ void __launch_bounds__(512, 3) w_trees(DevGraph g, WState s, int64_t 
             atomicSub(&sh_active, 1);
             polls = 0;
         };
-        // Lockstep: every iteration starts with a warp vote, so the 32 walkers
-        // of a warp each do one step per iteration (their memory accesses
-        // overlap) and a waiting walker polls once per iteration instead of
-        // spinning ahead of the others.  Finished walkers idle until the whole
-        // warp is done; errors end the loop for everyone through the vote.
+        // Lockstep: every tick starts with a warp vote, so a waiting walker
+        // polls once per tick instead of spinning ahead of the others.
+        // Finished walkers idle until the whole warp is done; errors end the
+        // loop for everyone through the vote.
         for (;;) {
             const bool err = vread(&sh_err) != 0;
             if (__any_sync(0xffffffffu, err)) break;
@@ -211,28 +214,44 @@ __global__ void __launch_bounds__(512, 3) w_trees(DevGraph g, WState s, int64_t 
             if (state == S_DONE) continue;
             if (DIAG) ++it_state[state];
             do {
+            // ---- transitions that touch no vertex word
+            bool hold = false;          // no vertex word this tick
+            if (state == S_WAITV) {
+                // after yielding: wait until the walker yielded to has moved on
+                if (vread(&ver[wait_on]) == wait_ver && vread(&prio[wait_on]) != INF) {
+                    if (waited_out()) break;
+                    hold = true;
+                } else {
+                    state = S_IDLE;
+                    polls = 0;
+                }
+            }
             if (state == S_IDLE) {
-                // a fresh start, else a requeued one
+                // the prefetched fresh start, else a fresh one, else a requeued one
                 int idx = -1;
-                if (vread(&sh_next) < nstart) {
-                    const int i = atomicAdd(&sh_next, 1);
-                    if (i < nstart) idx = i;
-                }
-                if (idx < 0) {
-                    const int hd = vread(&sh_rhead);
-                    if (hd < vread(&sh_rtail) && atomicCAS(&sh_rhead, hd, hd + 1) == hd) {
-                        int32_t *slot = rq + hd % nstart;
-                        uint64_t t0 = gtimer();
-                        int32_t v = ld32(slot);
-                        while (v == 0 && gtimer() - t0 < (uint64_t)max_wait_ns) v = ld32(slot);
-                        if (v == 0) { atomicOr(&sh_err, WERR_WAIT); break; }
-                        idx = v - 1;
-                        st32(slot, 0);
+                int32_t sv = -1;
+                if (pend_idx >= 0) {
+                    idx = pend_idx; sv = pend_start; pend_idx = -1;
+                } else {
+                    idx = take_fresh();
+                    if (idx < 0) {
+                        const int hd = vread(&sh_rhead);
+                        if (hd < vread(&sh_rtail) && atomicCAS(&sh_rhead, hd, hd + 1) == hd) {
+                            int32_t *slot = rq + hd % nstart;
+                            uint64_t t0 = gtimer();
+                            int32_t v = ld32(slot);
+                            while (v == 0 && gtimer() - t0 < (uint64_t)max_wait_ns) v = ld32(slot);
+                            if (v == 0) { atomicOr(&sh_err, WERR_WAIT); break; }
+                            idx = v - 1;
+                            st32(slot, 0);
+                        }
                     }
+                    if (idx >= 0) { sv = s.order[idx]; hold = true; }   // its word next tick
                 }
                 if (idx < 0) {
+                    // a premature "done" is harmless: a walker that requeues a
+                    // start takes it back itself when it becomes idle
                     const int act = vread(&sh_active);
-                    __threadfence_block();
                     if (act == 0 && vread(&sh_rhead) >= vread(&sh_rtail) && vread(&sh_next) >= nstart)
                         state = S_DONE;
                     else if (waited_out())
@@ -240,44 +259,61 @@ __global__ void __launch_bounds__(512, 3) w_trees(DevGraph g, WState s, int64_t 
                     continue;
                 }
                 polls = 0;
-                const int32_t sv = s.order[idx];
-                if (W_own(ldv(st + sv)) == OWN_SET) continue;
                 start = sv; head = -1; myprio = idx;
+                *(volatile int *)&kill[me] = -1;
                 atomicAdd(&sh_active, 1);
                 *(volatile int *)&prio[me] = idx;
                 bump();
                 state = S_WALK;
-                continue;
+                // fetch the next fresh start now; it is used when this walk ends
+                const int ni = take_fresh();
+                if (ni >= 0) { pend_idx = ni; pend_start = s.order[ni]; }
             }
-            if (state == S_WAITV) {
-                // after yielding: wait until the walker yielded to has moved on
-                if (vread(&ver[wait_on]) == wait_ver && vread(&prio[wait_on]) != INF) {
-                    if (waited_out()) break;
+            if (state == S_WALK && !hold && vread(&kill[me]) == myprio) {
+                // an earlier walk asked for a vertex of this path: release it
+                const int kb = vread(&killer[me]);
+                const int kv = vread(&killv[me]);
+                *(volatile int *)&kill[me] = -1;
+                wait_on = kb;
+                if (kb >= 0) wait_ver = vread(&ver[kb]);
+                cut = -1;
+                if (head >= 0 && kv >= 0 && kv < n) {
+                    // free the requested vertex first (checked on its load)
+                    cut = kv; cur = kv; walked = 0; state = S_REL;
+                } else if (head >= 0) {
+                    cur = start; walked = 0; state = S_REL;
                 } else {
-                    state = S_IDLE;
-                    polls = 0;
+                    drop_start(true);
+                    state = (wait_on >= 0 && must_wait()) ? S_WAITV : S_IDLE;
+                    continue;
                 }
-                continue;
             }
-            if (state == S_WAITH) {
-                // wait policy: the head's successor lies on an earlier walk's
-                // path; keep this path and wait until that vertex changes owner
-                // (a request to yield is served from here too)
-                const int32_t xw = head < 0 ? start : hp;
-                if (vread(&kill[me]) != myprio && W_own(ldv(st + xw)) == (uint32_t)wait_on) {
-                    if (waited_out()) break;
-                } else {
-                    state = S_WALK;
-                    polls = 0;
-                }
-                continue;
-            }
-            if (state == S_WAITK) {
-                // asked walker wait_on to yield the head's successor hp: wait
-                // until that vertex has left its path (it is freed first)
-                const int32_t xw = head < 0 ? start : hp;
-                if (W_own(ldv(st + xw)) == (uint32_t)wait_on && vread(&prio[wait_on]) == wait_prio &&
-                    vread(&kill[me]) != myprio) {
+            if (hold) continue;
+
+            // ---- the vertex word of this tick, and the row of a possible draw
+            int32_t a = -1, dv = -1;
+            if (state == S_WALK || state == S_WAITK || state == S_WAITH) a = head < 0 ? start : hp;
+            else if (state == S_POP || state == S_REL || state == S_SET) a = cur;
+            if (state == S_WALK) dv = a;
+            else if (state == S_POP && cur == head) dv = popx;
+            if (a < 0) continue;
+            const uint64_t w = ldv(st + a);
+            int64_t rb = 0;
+            uint32_t deg = 0;
+            if (dv >= 0) row_bounds<OFF64>(g, dv, rb, deg);
+
+            // ---- decide: at most one store, one CAS and one draw
+            int32_t s_v = -1;  uint64_t s_val = 0;               // store
+            int32_t c_v = -1;  uint64_t c_cmp = 0, c_val = 0;    // claim CAS
+            int32_t d_u = -1;  uint32_t d_k = 0;                 // draw succ(d_u, d_k)
+            int after = 0;     // 1: claim, 2: end of a pop, 3/4: end of a release/settle
+            if (state == S_WAITK || state == S_WAITH) {
+                // WAITK: asked walker wait_on to yield the vertex a; WAITH (wait
+                // policy): a lies on an earlier walk's path.  Wait until a has
+                // left that path (a request to yield is served from WALK).
+                bool still = W_own(w) == (uint32_t)wait_on && vread(&kill[me]) != myprio;
+                if (state == S_WAITK) still = still && vread(&prio[wait_on]) == wait_prio;
+                if (still) {
                     if (waited_out()) break;
                 } else {
                     state = S_WALK;
@@ -286,34 +322,27 @@ __global__ void __launch_bounds__(512, 3) w_trees(DevGraph g, WState s, int64_t 
                 continue;
             }
             if (state == S_POP) {
-                // one vertex of the loop popx -> ... -> head
-                const uint64_t wy = ldv(st + cur);
-                const int32_t nx = (int32_t)W_p(wy);
-                const uint32_t k = W_k(wy) + 1u;
+                // one vertex of the loop popx -> ... -> head (popx itself was
+                // done by the walk step that found the loop)
+                const uint32_t k = W_k(w) + 1u;
                 if (k > K_MAX) { atomicOr(&sh_err, WERR_KOVF); break; }
-                if (W_own(wy) != me || ++walked > n) { atomicOr(&sh_err, WERR_LOOP); break; }
+                if (W_own(w) != me || ++walked > n) { atomicOr(&sh_err, WERR_LOOP); break; }
                 ++pops;
-                if (cur == popx) kx = k;
-                else stv(st + cur, W_pack(P_INVALID, k, OWN_FREE));
-                if (cur == head) {
-                    const int32_t px = succ<OFF64, WT>(g, popx, kx, tree, 0u, k0, k1);
-                    stv(st + popx, W_pack((uint32_t)px, kx, me));
-                    head = popx; hp = px;
-                    bump();
-                    state = S_WALK;
-                } else {
-                    cur = nx;
-                }
-                continue;
-            }
-            if (state == S_REL || state == S_SET) {
+                s_v = cur; s_val = W_pack(P_INVALID, k, OWN_FREE);
+                if (cur == head) { d_u = popx; d_k = kx; after = 2; }
+                else cur = (int32_t)W_p(w);
+            } else if (state == S_REL || state == S_SET) {
                 // one vertex of the path.  SET: start -> head.  REL: when a
                 // walker asked for vertex `cut`, first cut -> head, then
                 // start -> the vertex before cut; otherwise start -> head.
-                const uint64_t wy = ldv(st + cur);
-                if (W_own(wy) != me || ++walked > n) { atomicOr(&sh_err, WERR_LOOP); break; }
-                stv(st + cur, (wy & ~OWN_MASK) | (state == S_REL ? OWN_FREE : OWN_SET));
-                const int32_t nxt = (int32_t)W_p(wy);
+                if (state == S_REL && cut >= 0 && cur == cut && head != -2 && W_own(w) != me) {
+                    // the requested vertex has left the path meanwhile
+                    cut = -1; cur = start; walked = 0;
+                    continue;
+                }
+                if (W_own(w) != me || ++walked > n) { atomicOr(&sh_err, WERR_LOOP); break; }
+                s_v = cur; s_val = (w & ~OWN_MASK) | (state == S_REL ? OWN_FREE : OWN_SET);
+                const int32_t nxt = (int32_t)W_p(w);
                 bool last = false;
                 if (state == S_REL && cut >= 0) {
                     if (cur == head) {           // end of the suffix pass
@@ -329,79 +358,86 @@ __global__ void __launch_bounds__(512, 3) w_trees(DevGraph g, WState s, int64_t 
                 } else {
                     cur = nxt;
                 }
-                if (!last) continue;
-                cut = -1;
-                if (state == S_REL) {
-                    drop_start(true);
-                    state = wait_on >= 0 ? S_WAITV : S_IDLE;
-                } else {
-                    drop_start(false);
-                    state = S_IDLE;
-                }
-                continue;
-            }
-            // S_WALK: one step of the loop-erased walk
-            if (vread(&kill[me]) == myprio) {
-                const int kb = vread(&killer[me]);
-                const int kv = vread(&killv[me]);
-                *(volatile int *)&kill[me] = -1;
-                wait_on = kb;
-                if (kb >= 0) wait_ver = vread(&ver[kb]);
-                cut = -1;
-                if (head >= 0 && kv >= 0 && kv < n && W_own(ldv(st + kv)) == me) {
-                    // free the requested vertex first
-                    cut = kv; cur = kv; walked = 0; state = S_REL;
-                } else if (head >= 0) { cur = start; walked = 0; state = S_REL; }
-                else { drop_start(true); state = wait_on >= 0 ? S_WAITV : S_IDLE; }
-                continue;
-            }
-            const int32_t x = head < 0 ? start : hp;
-            const uint64_t wx = ldv(st + x);
-            const uint32_t ox = W_own(wx);
-            ++steps;
-            if (ox == OWN_SET) {
-                if (head >= 0) { cur = start; walked = 0; state = S_SET; }
-                else { drop_start(false); state = S_IDLE; }
-                continue;
-            }
-            if (ox == me) {
-                cur = x; popx = x; walked = 0;
-                state = S_POP;
-                continue;
-            }
-            if (ox == OWN_FREE) {
-                // the successor draw does not depend on the claim: its loads are
-                // issued before the CAS result is used, so the two overlap
-                const bool draw = W_p(wx) == P_INVALID;
-                const int32_t px = draw ? succ<OFF64, WT>(g, x, W_k(wx), tree, 0u, k0, k1)
-                                        : (int32_t)W_p(wx);
-                const uint64_t claimed = (wx & ~OWN_MASK) | me;
-                if (cas_cta(st + x, wx, claimed) != wx) continue;
-                hp = px;
-                if (draw) stv(st + x, W_pack((uint32_t)hp, W_k(wx), me));
-                head = x;
-                bump();
-                continue;
-            }
-            // x is on another walker's path: the later walk yields
-            const int op = vread(&prio[ox]);
-            if (op == INF) continue;   // the owner has just dropped its walk: look again
-            if (myprio < op) {
-                *(volatile int *)&killer[ox] = (int)me;
-                *(volatile int *)&killv[ox] = x;
-                __threadfence_block();
-                *(volatile int *)&kill[ox] = op;
-                wait_on = (int)ox; wait_prio = op; polls = 0;
-                state = S_WAITK;
-            } else if (wait_policy) {
-                wait_on = (int)ox; polls = 0;
-                state = S_WAITH;
+                if (last) after = state == S_REL ? 3 : 4;   // the walk ends after the store
             } else {
-                wait_on = (int)ox;
-                wait_ver = vread(&ver[ox]);
+                // S_WALK: one step of the loop-erased walk from the head
+                const int32_t x = a;
+                const uint32_t ox = W_own(w);
+                ++steps;
+                if (ox == OWN_SET) {
+                    if (head >= 0) { cur = start; walked = 0; state = S_SET; }
+                    else { drop_start(false); state = S_IDLE; }
+                } else if (ox == me) {
+                    // x -> ... -> head -> x is a cycle: pop it, x first (x stays
+                    // on the path and gets its new successor at the end)
+                    const uint32_t k = W_k(w) + 1u;
+                    if (k > K_MAX) { atomicOr(&sh_err, WERR_KOVF); break; }
+                    ++pops;
+                    kx = k; popx = x; walked = 1;
+                    cur = (int32_t)W_p(w);
+                    state = S_POP;
+                } else if (ox == OWN_FREE) {
+                    c_v = x; c_cmp = w; c_val = (w & ~OWN_MASK) | me;
+                    if (W_p(w) == P_INVALID) { d_u = x; d_k = W_k(w); }
+                    after = 1;
+                } else {
+                    // x is on another walker's path: the later walk yields
+                    const int op = vread(&prio[ox]);
+                    if (op == INF) {
+                        // the owner has just dropped its walk: look again
+                    } else if (myprio < op) {
+                        *(volatile int *)&killer[ox] = (int)me;
+                        *(volatile int *)&killv[ox] = x;
+                        __threadfence_block();
+                        *(volatile int *)&kill[ox] = op;
+                        wait_on = (int)ox; wait_prio = op; polls = 0;
+                        state = S_WAITK;
+                    } else if (wait_policy & 1) {
+                        wait_on = (int)ox; polls = 0;
+                        state = S_WAITH;
+                    } else {
+                        wait_on = (int)ox;
+                        wait_ver = vread(&ver[ox]);
+                        cut = -1;
+                        if (head >= 0) { cur = start; walked = 0; state = S_REL; }
+                        else { drop_start(true); state = must_wait() ? S_WAITV : S_IDLE; }
+                    }
+                }
+            }
+
+            // ---- memory: store, claim (in flight during the draw), draw
+            if (s_v >= 0) stv(st + s_v, s_val);
+            uint64_t old = 0;
+            if (c_v >= 0) old = cas_cta(st + c_v, c_cmp, c_val);
+            int32_t px = -1;
+            if (d_u >= 0) {
+                const Ctr4 o = philox4x32_10(Ctr4{d_k, (uint32_t)d_u, tree, 0u}, k0, k1);
+                const uint32_t j = __umulhi(o.x, deg);
+                if (WT) {
+                    const WArc arc = g.warc[rb + j];
+                    px = (o.y < arc.thr) ? arc.col : arc.alias_col;
+                } else {
+                    px = __ldg(g.col + rb + j);
+                }
+            }
+            if (after == 1) {
+                if (old == c_cmp) {
+                    // claimed: x becomes the head
+                    hp = d_u >= 0 ? px : (int32_t)W_p(c_cmp);
+                    if (d_u >= 0) stv(st + c_v, W_pack((uint32_t)px, W_k(c_cmp), me));
+                    head = c_v;
+                    bump();
+                }
+                // a failed claim looks again next tick
+            } else if (after == 2) {
+                stv(st + popx, W_pack((uint32_t)px, kx, me));
+                head = popx; hp = px;
+                bump();
+                state = S_WALK;
+            } else if (after >= 3) {
                 cut = -1;
-                if (head >= 0) { cur = start; walked = 0; state = S_REL; }
-                else { drop_start(true); state = S_WAITV; }
+                drop_start(after == 3);
+                state = (after == 3 && wait_on >= 0 && must_wait()) ? S_WAITV : S_IDLE;
             }
             } while (0);
         }
@@ -492,15 +528,9 @@ rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, 
         B = (int64_t)std::max<size_t>(1, budget / per_tree);
     }
     B = std::min(B, T);
-    // walkers per tree: fill the GPU's resident threads with the chunk's trees
-    int W = o.block_threads;
-    if (W <= 0) {
-        const int64_t threads = (int64_t)num_sms() * 2048;
-        const int64_t want = threads / std::max<int64_t>(1, B);
-        W = 64;
-        while (W < 512 && 2 * W <= want) W *= 2;
-    }
-    W = std::max(32, std::min(512, W / 32 * 32));   // the kernel is built for <= 512 threads
+    // walkers per tree: chosen per launch below (the largest block that keeps
+    // every tree of the chunk resident at once, so no tree waits for a wave)
+    int W = o.block_threads > 0 ? std::max(32, std::min(512, o.block_threads / 32 * 32)) : 0;
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     void *buf = nullptr;
     const size_t bytes = (size_t)B * n * 8 + (size_t)B * (n - 1) * 4 + 256;
@@ -541,14 +571,25 @@ rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, 
         dispatch(g, [&](auto off64, auto wt) {
             auto kern = (o.profile >= 2) ? w_trees<decltype(off64)::value, decltype(wt)::value, true>
                                          : w_trees<decltype(off64)::value, decltype(wt)::value, false>;
-            const size_t smem = 5 * (size_t)W * sizeof(int);
-            int per_sm = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W, smem);
+            int Wc = W, per_sm = 0;
+            if (Wc == 0) {
+                // largest power of two in [64, 512] whose resident blocks cover
+                // the chunk; 64 when none does (the chunk then runs in waves)
+                Wc = 64;
+                for (int cand = 512; cand >= 64; cand /= 2) {
+                    int ps = 0;
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, kern, cand, 5 * (size_t)cand * sizeof(int));
+                    if ((int64_t)sms * ps >= Bc) { Wc = cand; break; }
+                }
+            }
+            const size_t smem = 5 * (size_t)Wc * sizeof(int);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Wc, smem);
             if (per_sm < 1) { status = set_error(RWC_ERR_UNSUPPORTED, "walker block does not fit"); return; }
             const int64_t blocks = std::min<int64_t>(Bc, (int64_t)sms * per_sm);
+            if (st) st->block_threads = Wc;
             ::rwc::count_launches(1);
-            kern<<<(unsigned)blocks, W, smem, stream>>>(g, ws, Bc, (uint32_t)(tree0 + c0), k0, k1, max_wait,
-                                                        o.walker_policy == 2 ? 1 : 0);
+            kern<<<(unsigned)blocks, Wc, smem, stream>>>(g, ws, Bc, (uint32_t)(tree0 + c0), k0, k1, max_wait,
+                                                         o.walker_policy == 2 ? 1 : o.walker_policy == 3 ? 2 : 0);
         });
         RWC_TRY(status);
         if (prof) cudaEventRecord(ev[2], stream);

@@ -48,7 +48,9 @@ MODES = {"shared": rwc.Options(mode=rwc.MODE_SHARED),
          "walker_w32_chunk5": rwc.Options(mode=rwc.MODE_WALKER, block_threads=32, trees_per_chunk=5),
          "walker_w1024": rwc.Options(mode=rwc.MODE_WALKER, block_threads=1024),
          "walker_yield": rwc.Options(mode=rwc.MODE_WALKER, walker_policy=1),
-         "walker_yield_w32": rwc.Options(mode=rwc.MODE_WALKER, walker_policy=1, block_threads=32)}
+         "walker_yield_w32": rwc.Options(mode=rwc.MODE_WALKER, walker_policy=1, block_threads=32),
+         "walker_fresh": rwc.Options(mode=rwc.MODE_WALKER, walker_policy=3),
+         "walker_fresh_w32": rwc.Options(mode=rwc.MODE_WALKER, walker_policy=3, block_threads=32)}
 
 
 @pytest.mark.parametrize("mode", list(MODES))
@@ -57,7 +59,8 @@ def test_special_graphs_bit_exact(gname, mode):
     assert_exact(SPECIAL[gname](), 37, MODES[mode])
 
 
-@pytest.mark.parametrize("mode", ["shared", "global", "global_chunk3", "walker", "walker_w32_chunk5"])
+@pytest.mark.parametrize("mode", ["shared", "global", "global_chunk3", "walker", "walker_w32_chunk5",
+                                  "walker_fresh"])
 def test_small_ba_config_bit_exact(mode):
     """BA n=2000, 3 edges per node + Hamiltonian path, unit weights, 1000
     trees, Philox seed 1: every tree identical to the oracle's."""
@@ -68,13 +71,14 @@ def test_small_ba_config_bit_exact(mode):
     assert_exact(g, 1000, opt)
 
 
-@pytest.mark.parametrize("mode", ["global", "global_nojump", "walker", "walker_w64", "walker_yield"])
+@pytest.mark.parametrize("mode", ["global", "global_nojump", "walker", "walker_w64", "walker_yield",
+                                  "walker_wait", "walker_fresh"])
 def test_grid_several_chunks_bit_exact(mode):
     g = synth.grid2d(61, 67)
     if mode.startswith("walker"):
+        pol = {"walker_yield": 1, "walker_wait": 2, "walker_fresh": 3}.get(mode, 0)
         opt = rwc.Options(mode=rwc.MODE_WALKER, trees_per_chunk=9,
-                          block_threads=64 if mode == "walker_w64" else 0,
-                          walker_policy=1 if mode == "walker_yield" else 0)
+                          block_threads=64 if mode == "walker_w64" else 0, walker_policy=pol)
     else:
         opt = rwc.Options(mode=rwc.MODE_GLOBAL, trees_per_chunk=9,
                           use_jumps=0 if mode == "global_nojump" else -1)
