@@ -1,0 +1,65 @@
+"""Pins of the automatic parameters (Section 5): the spectral radius of P_v
+against closed forms, the double-sweep diameter against all-pairs BFS, and
+the sample-size and solver-accuracy formulas on hand-evaluated instances."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import params as op
+
+
+@pytest.mark.parametrize("n", [3, 4, 7, 12])
+def test_lambda_complete_graph(n):
+    # P_v on K_n minus v: (J - I) / (n - 1) on n - 1 vertices; Perron root (n-2)/(n-1)
+    assert op.spectral_radius_pv(synth.complete(n), 0) == pytest.approx((n - 2) / (n - 1), abs=1e-13)
+
+
+@pytest.mark.parametrize("n", [3, 5, 10, 33])
+def test_lambda_cycle(n):
+    # C_n minus v is a path of n-1 vertices whose ends both step into v with
+    # probability 1/2: P_v = tridiag(1/2, 0, 1/2), spectral radius cos(pi/n)
+    assert op.spectral_radius_pv(synth.cycle(n), 3 % n) == pytest.approx(math.cos(math.pi / n), abs=1e-13)
+
+
+def test_lambda_star_centre_and_leaf():
+    g = synth.star(20, center=0)
+    assert op.spectral_radius_pv(g, 0) == pytest.approx(0.0, abs=1e-15)
+    # rooted at a leaf: the rest is a star of 18 leaves around the centre,
+    # whose centre steps back to a leaf with probability 18/19 (radius sqrt(18/19))
+    assert op.spectral_radius_pv(g, 5) == pytest.approx(math.sqrt(18 / 19), abs=1e-13)
+
+
+def _diameter(g):
+    return max(int(op.bfs_dist(g, s).max()) for s in range(g.n))
+
+
+@pytest.mark.parametrize("gname", ["path", "grid", "tree", "ba", "cycle"])
+def test_double_sweep(gname):
+    g = {"path": lambda: synth.path(40),
+         "grid": lambda: synth.grid2d(7, 11),
+         "tree": lambda: synth.star(15, center=4),
+         "ba": lambda: synth.ba(300, 2, seed=1),
+         "cycle": lambda: synth.cycle(21)}[gname]()
+    a, delta = op.double_sweep(g, 0)
+    assert op.bfs_dist(g, 0)[a] == op.bfs_dist(g, 0).max()
+    if gname in ("path", "grid", "tree", "cycle"):
+        assert delta == _diameter(g)
+    else:
+        assert delta <= _diameter(g)
+    if gname == "grid":
+        assert delta == 7 + 11 - 2
+
+
+def test_formulas_hand_evaluated():
+    # K_4 rooted at 0: n = 4, m = 6, d = 3, ||d_-v|| = sqrt(27), lambda = 2/3
+    t = op.walk_bound(4, 6.0, math.sqrt(27.0), 2.0 / 3.0)
+    assert t == pytest.approx(math.log(1.0 / 6.0) / math.log(2.0 / 3.0), rel=1e-15)
+    assert op.tree_count(0.1, 4, t) == math.ceil(200.0 * t * t * math.log(8.0))
+    # theta for n = 4, m = 6, dmax = 3, Delta = 1: eps / (2 * 3 * (1 + 15/12)^2 * sqrt(24))
+    assert op.solver_theta(0.1, 4, 6.0, 3.0, 1) == pytest.approx(0.1 / (6.0 * 2.25 ** 2 * math.sqrt(24.0)), rel=1e-15)
+    assert op.walk_bound(5, 4.0, 2.0, 0.0) == 1.0
+    p = op.auto_params(synth.complete(4), 0, 0.1)
+    assert p["diameter"] == 1 and p["lambda"] == pytest.approx(2 / 3, abs=1e-13)
+    assert p["trees"] == op.tree_count(0.1, 4, p["t"])
