@@ -109,8 +109,10 @@ typedef struct {
 typedef struct {
     int64_t trees;        /* trees sampled by the last call */
     int64_t draws;        /* successor draws (= sum of visits over all trees) */
-    int64_t rounds;       /* GLOBAL/SHARED: popping rounds; WALKER: yielded walks */
-    int64_t walk_steps;   /* GLOBAL: pointer-chasing steps; WALKER: walker steps */
+    int64_t rounds;       /* GLOBAL/SHARED: popping rounds; WALKER: yielded walks
+                             (counted with rwc_options_t.profile = 2 only) */
+    int64_t walk_steps;   /* GLOBAL: pointer-chasing steps; WALKER: walker steps
+                             (profile = 2 only) */
     int64_t chunks;       /* tree chunks processed */
     int32_t mode;         /* mode actually used */
     int32_t block_threads; /* WALKER: walkers (threads) per tree of the last chunk */
@@ -226,11 +228,11 @@ rwc_status rwc_sample_trees_noalloc(rwc_graph_t *g, uint64_t seed, int64_t tree0
 /*
  * Algorithm 1 (AppRWC) fed by the estimator of Section 5.
  *   t_u = sums[u] / num_trees                        (estimate of (NL_v^-1)_uu)
- *   b   = sqrt(d_v) e_v - (sqrt(d_v) / vol) d        (line 1)
+ *   b   = sqrt(d_v) e_v - (sqrt(d_v) / vol) d        (right-hand side)
  *   z   = L^+ b by Jacobi-preconditioned CG to relative residual cg_tol
- *         (line 2, the paper's LapSolve; FP32 SpMV inner solves, FP64
- *         residual refinement, z kept in FP64)
- *   y_u = sqrt(d_u) z_u - sqrt(d_u) (sum_w d_w z_w) / vol   (line 3)
+ *         (the paper's LapSolve; FP32 SpMV inner solves, FP64 residual
+ *         refinement, z kept in FP64)
+ *   y_u = sqrt(d_u) z_u - sqrt(d_u) (sum_w d_w z_w) / vol   (pivot column)
  *   H_u = (t_u - (d_u/d_v) y_v + 2 sqrt(d_u/d_v) y_u) / pi_u, u != v (Eq. 3)
  *   H_v = y_v / pi_v
  * sums: FP64 [n] device; H_out: FP64 [n] device; y_out: NULL or FP64 [n].
@@ -242,7 +244,7 @@ rwc_status rwc_estimate(rwc_graph_t *g, const double *sums, int64_t num_trees,
                         rwc_stream_t stream);
 
 /*
- * Recovery step only (Algorithm 1 lines 4-7) for a given pivot column y
+ * Recovery step only (Algorithm 1, the recovery of H from t and y) for a given pivot column y
  * (FP64 [n] device): H from sums/num_trees and y as in rwc_estimate.
  */
 rwc_status rwc_recover(rwc_graph_t *g, const double *sums, int64_t num_trees,
@@ -306,6 +308,64 @@ rwc_status rwc_batch_roots(const rwc_batch_t *b, int32_t *host_roots);
  * the device; results are cached in cache_path (JSON, may be NULL). */
 rwc_status rwc_autotune(rwc_batch_t *b, const char *cache_path, rwc_stream_t stream);
 rwc_status rwc_batch_destroy(rwc_batch_t *b);
+
+/*
+ * Automatic parameters (Section 5, "The Sampling Algorithm": the sample size
+ * of the tree-count lemma and the solver accuracy of the performance theorem).
+ *
+ *   lambda = spectral radius of P_v (D^-1 W without the pivot's row and
+ *            column), by inverse iteration on the normalised grounded
+ *            Laplacian I - D^-1/2 W D^-1/2 restricted to V \ {v}; mu = 1 - lambda
+ *   diameter = BFS double sweep from the pivot (a lower bound on Delta,
+ *            exact on trees and grids); sweep_end = the vertex it starts the
+ *            second sweep from (farthest from the pivot, smallest id on ties)
+ *   t      = log(m / (n sqrt(n-1) |d_-v|_2)) / log(lambda), at least 1
+ *            (m = vol / 2; walks longer than t are rarer than 1/n)
+ *   trees  = ceil(2 t^2 log(2n) / eps^2)
+ *   theta  = eps / (2 Delta d_max (1 + d_max (1 + n) / (2m))^2 sqrt(m n Delta))
+ *
+ * max_iters (<= 0: 30) and tol (<= 0: 1e-9) bound the inverse iteration,
+ * which stops when mu changes by at most tol relative.  Each iteration is one
+ * Laplacian solve.  Synchronises stream.
+ */
+typedef struct {
+    double lambda;
+    double mu;
+    double t;
+    double theta;
+    int64_t trees;
+    int64_t diameter;
+    int32_t sweep_end;
+    int32_t iterations;
+} rwc_params_t;
+
+rwc_status rwc_auto_params(rwc_graph_t *g, double eps, int32_t max_iters, double tol,
+                           rwc_params_t *out, rwc_stream_t stream);
+
+/*
+ * Evaluation measures (Section 6, "Evaluation Measures" and "Approximation
+ * Quality").
+ *
+ * rwc_mre: mean relative error (1/n) sum_u |H_u - H_est_u| / H_u of an
+ * estimate against a reference.  H, H_est: device FP64 [n], H_u != 0.
+ * out: device FP64 scalar, written (not accumulated).  The reduction order is
+ * fixed, so repeated calls give identical results.  n >= 1.  Asynchronous on
+ * stream.
+ */
+rwc_status rwc_mre(int64_t n, const double *H, const double *H_est, double *out,
+                   rwc_stream_t stream);
+
+/*
+ * rwc_kendall: Kendall distance of the rankings given by a and b,
+ * K = 2 (alpha - beta) / (n (n - 1)), alpha / beta the concordant /
+ * discordant pairs; a pair tied in a or in b counts neither way (Kendall's
+ * tau-a).  a, b: device FP64 [n], no NaN (-0.0 equals +0.0).  out_diff:
+ * device int64 scalar, written with alpha - beta (exact).  host_tau: NULL, or
+ * a host double receiving K (then the call synchronises stream).  Every pair
+ * is compared, O(n^2) work: 0 <= n <= 2^26.
+ */
+rwc_status rwc_kendall(int64_t n, const double *a, const double *b, int64_t *out_diff,
+                       double *host_tau, rwc_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -16,8 +16,8 @@ diameter Delta they need.  Test infrastructure only; FP64.
   expected fraction of walks not yet trapped at v is below beta.  Reading
   (the printed argument is ambiguous about where ||d_-v||_2 stands): it
   divides, so that lambda^t <= beta m / (sqrt(n-s) ||d_-v||_2); weighted
-  graphs use m = vol / 2 and d = weighted degrees.  lambda = 0 (every walk is
-  trapped in one step) gives t = 1.
+  graphs use m = vol / 2 and d = weighted degrees.  t is at least 1 (a walk
+  takes a step), which also covers lambda = 0 (every walk trapped at once).
 * l = ceil( 2 t^2 log(2n) / eps^2 )  (the tree-count lemma).
 * theta = eps / ( 2 Delta d_max (1 + d_max (1 + n) / (2m))^2 sqrt(m n Delta) ).
 
@@ -82,9 +82,10 @@ def spectral_radius_pv(g, v: int) -> float:
 
 
 def walk_bound(n: int, m: float, d_minus_v_norm: float, lam: float) -> float:
+    """t, at least one step."""
     if lam <= 0.0:
         return 1.0
-    return math.log(m / (n * math.sqrt(n - 1) * d_minus_v_norm)) / math.log(lam)
+    return max(1.0, math.log(m / (n * math.sqrt(n - 1) * d_minus_v_norm)) / math.log(lam))
 
 
 def tree_count(eps: float, n: int, t: float) -> int:

@@ -42,6 +42,17 @@ class Options(ctypes.Structure):
                          memory_budget, profile, walker_policy)
 
 
+class Params(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("mu", ctypes.c_double), ("t", ctypes.c_double),
+                ("theta", ctypes.c_double), ("trees", ctypes.c_int64), ("diameter", ctypes.c_int64),
+                ("sweep_end", ctypes.c_int32), ("iterations", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {"lambda": self.lambda_, "mu": self.mu, "t": self.t, "theta": self.theta,
+                "trees": self.trees, "diameter": self.diameter, "sweep_end": self.sweep_end,
+                "iterations": self.iterations}
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("trees", ctypes.c_int64), ("draws", ctypes.c_int64), ("rounds", ctypes.c_int64),
                 ("walk_steps", ctypes.c_int64), ("chunks", ctypes.c_int64), ("mode", ctypes.c_int32),
@@ -90,6 +101,9 @@ def lib():
         "rwc_batch_roots": ([_vp, _vp], _i32),
         "rwc_autotune": ([_vp, ctypes.c_char_p, _vp], _i32),
         "rwc_batch_destroy": ([_vp], _i32),
+        "rwc_mre": ([_i64, _vp, _vp, _vp, _vp], _i32),
+        "rwc_auto_params": ([_vp, _d, _i32, _d, ctypes.POINTER(Params), _vp], _i32),
+        "rwc_kendall": ([_i64, _vp, _vp, _vp, ctypes.POINTER(_d), _vp], _i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -259,3 +273,39 @@ def rwc_autotune(b, cache_path=None, stream=None):
 
 def rwc_batch_destroy(b):
     _check(lib().rwc_batch_destroy(b))
+
+
+def rwc_auto_params(g, eps, max_iters=0, tol=0.0, stream=None) -> Params:
+    """Sample size, solver accuracy, lambda and diameter for graph g."""
+    p = Params()
+    _check(lib().rwc_auto_params(g, float(eps), int(max_iters), float(tol), ctypes.byref(p),
+                                 _stream(stream)))
+    return p
+
+
+def rwc_mre(H, H_est, out=None, stream=None):
+    """Mean relative error of H_est against H (device FP64 [n]); returns the
+    device scalar ``out`` (allocated when None)."""
+    import torch
+    n = H.numel()
+    if H_est.numel() != n:
+        raise ValueError("H and H_est differ in length")
+    if out is None:
+        out = torch.empty((), dtype=torch.float64, device=H.device)
+    _check(lib().rwc_mre(n, _dptr(H, torch.float64, "H"), _dptr(H_est, torch.float64, "H_est"),
+                         _dptr(out, torch.float64, "out"), _stream(stream)))
+    return out
+
+
+def rwc_kendall(a, b, stream=None):
+    """Kendall distance K of the rankings a, b (device FP64 [n]) and the exact
+    alpha - beta; returns (K, alpha_minus_beta)."""
+    import torch
+    n = a.numel()
+    if b.numel() != n:
+        raise ValueError("a and b differ in length")
+    diff = torch.empty((), dtype=torch.int64, device=a.device)
+    tau = ctypes.c_double(0.0)
+    _check(lib().rwc_kendall(n, _dptr(a, torch.float64, "a"), _dptr(b, torch.float64, "b"),
+                             _dptr(diff, torch.int64, "out_diff"), ctypes.byref(tau), _stream(stream)))
+    return tau.value, int(diff.item())

@@ -40,7 +40,7 @@ __global__ void dot64(int64_t n, const double *a, const double *b, double *out) 
     if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(out, s);
 }
 
-// Algorithm 1 line 1: b = sqrt(d_v) e_v - (sqrt(d_v) / vol) d.
+// Algorithm 1, right-hand side: b = sqrt(d_v) e_v - (sqrt(d_v) / vol) d.
 __global__ void rhs_pivot(int64_t n, const double *d, int32_t v, double vol, double *b) {
     const double sv = sqrt(d[v]);
     for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
@@ -48,7 +48,7 @@ __global__ void rhs_pivot(int64_t n, const double *d, int32_t v, double vol, dou
         b[u] = -(sv / vol) * d[u] + (u == v ? sv : 0.0);
 }
 
-// Algorithm 1 line 3: y_u = sqrt(d_u) z_u - sqrt(d_u) (sum_w d_w z_w) / vol.
+// Algorithm 1, pivot column: y_u = sqrt(d_u) z_u - sqrt(d_u) (sum_w d_w z_w) / vol.
 __global__ void y_from_z(int64_t n, const double *d, const double *z, const double *dz, double vol,
                          double *y) {
     const double m = *dz / vol;
@@ -59,7 +59,7 @@ __global__ void y_from_z(int64_t n, const double *d, const double *z, const doub
     }
 }
 
-// Algorithm 1 lines 4-7 with t_u = sums_u / l (Section 5's estimator).
+// Algorithm 1, recovery, with t_u = sums_u / l (Section 5's estimator).
 __global__ void recover(int64_t n, const double *d, int32_t v, double vol, const double *sums,
                         double inv_l, const double *y, double *H) {
     const double dv = d[v], yv = y[v];

@@ -275,6 +275,29 @@ static rwc_status create_impl(int64_t n, int64_t nnz, const int64_t *rp, const i
         if ((e = upload(G, &pdi, di.data(), (size_t)n)) != cudaSuccess) return fail(e, "inverse degrees");
         g.dinv32 = pdi;
     }
+    {
+        // chunks of the heavy rows (a row's chunks consecutive, rows in order)
+        std::vector<int32_t> crow, hf;
+        std::vector<int64_t> cbeg;
+        for (int64_t u = 0; u < n; ++u) {
+            const int64_t deg = rp[u + 1] - rp[u];
+            if (deg <= HEAVY_DEG) continue;
+            if (hf.empty()) hf.assign(n, -1);
+            hf[u] = (int32_t)crow.size();
+            for (int64_t j = rp[u]; j < rp[u + 1]; j += HEAVY_CHUNK) {
+                crow.push_back((int32_t)u);
+                cbeg.push_back(j);
+            }
+        }
+        if (!crow.empty()) {
+            int32_t *pr, *ph;
+            int64_t *pb;
+            if ((e = upload(G, &pr, crow.data(), crow.size())) != cudaSuccess) return fail(e, "heavy rows");
+            if ((e = upload(G, &pb, cbeg.data(), cbeg.size())) != cudaSuccess) return fail(e, "heavy rows");
+            if ((e = upload(G, &ph, hf.data(), hf.size())) != cudaSuccess) return fail(e, "heavy rows");
+            g.hc_n = (int64_t)crow.size(); g.hc_row = pr; g.hc_beg = pb; g.hfirst = ph;
+        }
+    }
     if ((e = cudaMallocHost((void **)&G->host_scalars, 64 * sizeof(int64_t))) != cudaSuccess)
         return fail(e, "pinned scalars");
     *out = G;

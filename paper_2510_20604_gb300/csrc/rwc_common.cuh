@@ -55,7 +55,16 @@ struct DevGraph {
     const double *d = nullptr;       // [n] weighted degrees
     const float *dinv32 = nullptr;   // [n] 1/d (Jacobi preconditioner)
     double vol = 0.0, dmax = 0.0;
+    // rows with more than HEAVY_DEG arcs, cut into chunks of HEAVY_CHUNK arcs
+    // so that a sparse product can give every chunk its own warp
+    int64_t hc_n = 0;                // chunks
+    const int32_t *hc_row = nullptr; // [hc_n] row of each chunk (a row's chunks are consecutive)
+    const int64_t *hc_beg = nullptr; // [hc_n] first arc of each chunk
+    const int32_t *hfirst = nullptr; // [n] first chunk of a heavy row, -1 for other rows
 };
+
+constexpr int64_t HEAVY_DEG = 1024;
+constexpr int64_t HEAVY_CHUNK = 1024;
 
 }  // namespace rwc
 

@@ -325,11 +325,16 @@ __global__ void inner_update(int64_t n, int k, const double *rz, const double *p
 // reads the same reduced values after a grid sync, so the loop exit (relative
 // residual at most tol, or no halving of <r,r> for `window` iterations, or
 // max_it) is taken by all blocks together.  out[0] = iterations, out[1] = last <r,r>.
+// Rows with more than HEAVY_DEG arcs are left out of the sub-warp product;
+// each of their HEAVY_CHUNK-arc chunks gets one warp, which stores its partial
+// sum in hsum and adds its share of <p, q> (p_u d_u p_u for a row's first
+// chunk, -p_u s_c for every chunk), and the update phase assembles such a
+// row's q_u = d_u p_u - sum of its chunks in chunk order.
 template <int VW, bool OFF64, bool W>
 __global__ void __launch_bounds__(TPB) cg1_coop(DevGraph g, const float *__restrict__ dinv,
                                                 float *r, float *e, float *z, float *p, float *q,
-                                                double *sc, int max_it, double tol2, int window,
-                                                double *out) {
+                                                float *hsum, double *sc, int max_it, double tol2,
+                                                int window, double *out) {
     cg::grid_group grid = cg::this_grid();
     const int sub = threadIdx.x & (VW - 1);
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -344,18 +349,40 @@ __global__ void __launch_bounds__(TPB) cg1_coop(DevGraph g, const float *__restr
         for (int64_t u0 = row0 - (row0 % (32 / VW)); u0 < g.n; u0 += nrows) {
             const int64_t u = u0 + (row0 % (32 / VW));
             float sacc = 0.f;
+            bool light = false;
             if (u < g.n) {
                 int64_t b, e2;
                 rowb<OFF64>(g, u, b, e2);
-                for (int64_t j = b + sub; j < e2; j += VW) sacc += (W ? g.w[j] : 1.f) * p[g.col[j]];
+                light = g.hc_n == 0 || e2 - b <= HEAVY_DEG;
+                if (light)
+                    for (int64_t j = b + sub; j < e2; j += VW) sacc += (W ? g.w[j] : 1.f) * p[g.col[j]];
             }
 #pragma unroll
             for (int o = VW / 2; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o, VW);
-            if (sub == 0 && u < g.n) {
+            if (sub == 0 && light) {
                 const float pu = p[u];
                 const float qu = (float)g.d[u] * pu - sacc;
                 q[u] = qu;
                 acc += (double)pu * (double)qu;
+            }
+        }
+        if (g.hc_n) {
+            const int lane = threadIdx.x & 31;
+            for (int64_t c = tid / 32; c < g.hc_n; c += nthr / 32) {
+                const int32_t u = g.hc_row[c];
+                int64_t rb0, re;
+                rowb<OFF64>(g, u, rb0, re);
+                const int64_t b = g.hc_beg[c], e2 = min(b + HEAVY_CHUNK, re);
+                float s = 0.f;
+                for (int64_t j = b + lane; j < e2; j += 32) s += (W ? g.w[j] : 1.f) * p[g.col[j]];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) {
+                    hsum[c] = s;
+                    const double pu = (double)p[u];
+                    if (b == rb0) acc += pu * (double)(float)((float)g.d[u] * p[u]);
+                    acc -= pu * (double)s;
+                }
             }
         }
         acc = warp_sum(acc);
@@ -366,8 +393,20 @@ __global__ void __launch_bounds__(TPB) cg1_coop(DevGraph g, const float *__restr
         const float a = (den > 0.0 && rz > 0.0) ? (float)(rz / den) : 0.f;
         double a1 = 0.0, a2 = 0.0;
         for (int64_t i = tid; i < g.n; i += nthr) {
+            float qi;
+            const int32_t hf = g.hc_n ? g.hfirst[i] : -1;
+            if (hf < 0) {
+                qi = q[i];
+            } else {
+                int64_t rb0, re;
+                rowb<OFF64>(g, i, rb0, re);
+                const int64_t nc = (re - rb0 + HEAVY_CHUNK - 1) / HEAVY_CHUNK;
+                float s = 0.f;
+                for (int64_t c = 0; c < nc; ++c) s += hsum[hf + c];
+                qi = (float)g.d[i] * p[i] - s;
+            }
             e[i] += a * p[i];
-            const float rv = r[i] - a * q[i];
+            const float rv = r[i] - a * qi;
             r[i] = rv;
             const float zv = dinv[i] * rv;
             z[i] = zv;
@@ -465,7 +504,8 @@ rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, doub
     const size_t fbytes = (size_t)nk * sizeof(float);
     const size_t sc_per_it = 3 * (size_t)k;                 // pq, rz, rr per iteration
     const size_t sc_count = (size_t)(max_inner + 4) * sc_per_it + 8 * (size_t)k;
-    const size_t bytes = (size_t)nk * sizeof(double) + 5 * fbytes + sc_count * sizeof(double) + 1024;
+    const size_t hbytes = (size_t)(g.hc_n + 1) * sizeof(float);
+    const size_t bytes = (size_t)nk * sizeof(double) + 5 * fbytes + sc_count * sizeof(double) + hbytes + 1024;
     RWC_CUDA_TRY(cudaMallocAsync(&buf.p, bytes, st));
     char *q = (char *)buf.p;
     double *R = (double *)q; q += (size_t)nk * sizeof(double);
@@ -477,6 +517,7 @@ rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, doub
     q = (char *)(((uintptr_t)q + 255) & ~(uintptr_t)255);
     double *outer_sc = (double *)q;       // [0,k) colsum, [k,2k) |R|^2, [2k,3k) |B|^2
     double *it_sc = outer_sc + 8 * (size_t)k;
+    float *hsum = (float *)(it_sc + (sc_count - 8 * (size_t)k));   // [hc_n] heavy-chunk sums
     const size_t shk = (size_t)k * sizeof(double), shk2 = 2 * shk;
     const unsigned gs = grid_for(nk), gw = grid_for(n * 32);
     const int vw = pick_vw(g);
@@ -540,10 +581,10 @@ rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, doub
                     if (per_sm < 1) return;
                     const unsigned blocks = (unsigned)std::min<int64_t>((int64_t)num_sms() * per_sm, gv);
                     const float *dinv = g.dinv32;
-                    float *rr_ = r, *ee = e, *zz = z, *pp = p, *qq = Qv;
+                    float *rr_ = r, *ee = e, *zz = z, *pp = p, *qq = Qv, *hs = hsum;
                     double *scp = it_sc;
                     DevGraph gg = g;
-                    void *args[] = {&gg, &dinv, &rr_, &ee, &zz, &pp, &qq, &scp, &mi, &t2, &window, &outv};
+                    void *args[] = {&gg, &dinv, &rr_, &ee, &zz, &pp, &qq, &hs, &scp, &mi, &t2, &window, &outv};
                     ::rwc::count_launches(1);
                     if (cudaLaunchCooperativeKernel((const void *)kern, blocks, TPB, args, 0, st) == cudaSuccess)
                         launched = true;

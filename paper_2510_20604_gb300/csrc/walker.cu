@@ -119,12 +119,19 @@ __device__ __forceinline__ uint64_t gtimer() {
 // states they are in.  Waits poll shared memory or the one vertex word.
 enum : int { S_IDLE = 0, S_WALK, S_POP, S_REL, S_SET, S_WAITK, S_WAITV, S_WAITH, S_DONE };
 
+// Register cap of the walker kernel: 46 registers are used without spills.
+// (A cap of 40 lets 96-walker blocks keep 2000 trees resident, but its
+// spills cost more than the extra walkers gain.)
+#ifndef RWC_WALKER_MAXNREG
+#define RWC_WALKER_MAXNREG 48
+#endif
+
 template <bool OFF64, bool WT, bool DIAG>
-__global__ void __launch_bounds__(512, 2) w_trees(DevGraph g, WState s, int64_t B, uint32_t tree0,
+__global__ void __maxnreg__(RWC_WALKER_MAXNREG) w_trees(DevGraph g, WState s, int64_t B, uint32_t tree0,
                                                 uint32_t k0, uint32_t k1, int64_t max_wait_ns,
                                                 int wait_policy) {
-    const int64_t n = g.n;
-    const int64_t nstart = n - 1;
+    const int n = (int)g.n;            // the host keeps n below 2^31 - 2
+    const int nstart = n - 1;
     const uint32_t me = threadIdx.x;
     constexpr int INF = 0x7fffffff;
     __shared__ int sh_tree;
@@ -165,8 +172,8 @@ __global__ void __launch_bounds__(512, 2) w_trees(DevGraph g, WState s, int64_t 
         int myprio = INF, wait_on = -1, wait_ver = 0, wait_prio = 0;
         int pend_idx = -1;            // next fresh start, fetched one walk ahead
         int32_t pend_start = -1;
-        int64_t walked = 0;          // vertices visited in the current POP/REL/SET pass
-        int64_t polls = 0;
+        int walked = 0;          // vertices visited in the current POP/REL/SET pass
+        uint32_t polls = 0;
         uint64_t wait_t0 = 0;
         auto vread = [](const int *a) { return *(const volatile int *)a; };
         auto bump = [&]() { *(volatile int *)&ver[me] = ver[me] + 1; };
@@ -195,7 +202,7 @@ __global__ void __launch_bounds__(512, 2) w_trees(DevGraph g, WState s, int64_t 
         auto drop_start = [&](bool requeue) {
             if (requeue) {
                 rq_push(rq, &sh_rtail, nstart, myprio);
-                ++yields;
+                if (DIAG) ++yields;
             }
             *(volatile int *)&prio[me] = INF;
             bump();
@@ -327,7 +334,7 @@ __global__ void __launch_bounds__(512, 2) w_trees(DevGraph g, WState s, int64_t 
                 const uint32_t k = W_k(w) + 1u;
                 if (k > K_MAX) { atomicOr(&sh_err, WERR_KOVF); break; }
                 if (W_own(w) != me || ++walked > n) { atomicOr(&sh_err, WERR_LOOP); break; }
-                ++pops;
+                if (DIAG) ++pops;
                 s_v = cur; s_val = W_pack(P_INVALID, k, OWN_FREE);
                 if (cur == head) { d_u = popx; d_k = kx; after = 2; }
                 else cur = (int32_t)W_p(w);
@@ -363,7 +370,7 @@ __global__ void __launch_bounds__(512, 2) w_trees(DevGraph g, WState s, int64_t 
                 // S_WALK: one step of the loop-erased walk from the head
                 const int32_t x = a;
                 const uint32_t ox = W_own(w);
-                ++steps;
+                if (DIAG) ++steps;
                 if (ox == OWN_SET) {
                     if (head >= 0) { cur = start; walked = 0; state = S_SET; }
                     else { drop_start(false); state = S_IDLE; }
@@ -372,7 +379,7 @@ __global__ void __launch_bounds__(512, 2) w_trees(DevGraph g, WState s, int64_t 
                     // on the path and gets its new successor at the end)
                     const uint32_t k = W_k(w) + 1u;
                     if (k > K_MAX) { atomicOr(&sh_err, WERR_KOVF); break; }
-                    ++pops;
+                    if (DIAG) ++pops;
                     kx = k; popx = x; walked = 1;
                     cur = (int32_t)W_p(w);
                     state = S_POP;
@@ -445,9 +452,9 @@ __global__ void __launch_bounds__(512, 2) w_trees(DevGraph g, WState s, int64_t 
         if (threadIdx.x == 0 && sh_err) atomicOr(s.err, sh_err);
         if (sh_err) break;
     }
-    if (steps) atomicAdd(&s.ctr[0], steps);
-    if (yields) atomicAdd(&s.ctr[1], yields);
-    if (pops) atomicAdd(&s.ctr[2], pops);
+    if (DIAG && steps) atomicAdd(&s.ctr[0], steps);
+    if (DIAG && yields) atomicAdd(&s.ctr[1], yields);
+    if (DIAG && pops) atomicAdd(&s.ctr[2], pops);
     if (DIAG && s.diag)
         for (int i = 0; i < 8; ++i) {
             const unsigned long long v = it_state[i] + (i == S_WAITV ? it_state[S_WAITH] : 0ull);
@@ -573,10 +580,10 @@ rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, 
                                          : w_trees<decltype(off64)::value, decltype(wt)::value, false>;
             int Wc = W, per_sm = 0;
             if (Wc == 0) {
-                // largest power of two in [64, 512] whose resident blocks cover
+                // largest multiple of 32 in [64, 512] whose resident blocks cover
                 // the chunk; 64 when none does (the chunk then runs in waves)
                 Wc = 64;
-                for (int cand = 512; cand >= 64; cand /= 2) {
+                for (int cand = 512; cand >= 64; cand -= 32) {
                     int ps = 0;
                     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, kern, cand, 5 * (size_t)cand * sizeof(int));
                     if ((int64_t)sms * ps >= Bc) { Wc = cand; break; }

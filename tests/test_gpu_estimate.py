@@ -14,11 +14,27 @@ from oracle import wilson as ow
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("gname", ["ba", "weighted", "grid"])
+def _hub_graph():
+    """A BA graph whose vertex 0 is also joined to 2500 others (a row of more
+    than 2 * 1024 arcs: the solver's chunked heavy-row path)."""
+    base = synth.ba(3000, 2, seed=4)
+    src, dst = base.src(), base.col
+    keep = src < dst
+    a = list(src[keep]); b = list(dst[keep])
+    have = set(b[i] for i in range(len(a)) if a[i] == 0)
+    for v in range(1, 2501):
+        if v not in have:
+            a.append(0); b.append(v)
+    return synth.from_edges(3000, np.array(a), np.array(b))
+
+
+@pytest.mark.parametrize("gname", ["ba", "weighted", "grid", "hub", "rmat13w"])
 def test_pivot_column_and_recovery(gname):
     g = {"ba": lambda: synth.ba(500, 3, seed=1),
          "weighted": lambda: synth.rgg(600, 10.0, seed=2, sigma=0.5),
-         "grid": lambda: synth.grid2d(20, 23)}[gname]()
+         "grid": lambda: synth.grid2d(20, 23),
+         "hub": _hub_graph,
+         "rmat13w": lambda: synth.rmat(13, 16, seed=3, sigma=1.0)}[gname]()
     G = rwc.Graph.from_synth(g)
     T = 200
     sums, _, _, _ = G.sample(T, seed=3)
@@ -34,6 +50,24 @@ def test_pivot_column_and_recovery(gname):
     H2 = torch.empty_like(H)
     rwc.rwc_recover(G.handle, sums, T, y, H2)
     assert torch.allclose(H, H2, rtol=1e-15, atol=0)
+
+
+def test_single_rhs_solve_with_heavy_rows():
+    """k = 1 takes the one-launch cooperative solver, whose sparse product
+    splits rows of more than 1024 arcs into warp-sized chunks."""
+    g = _hub_graph()
+    assert np.diff(g.row_ptr).max() > 2048
+    G = rwc.Graph.from_synth(g)
+    L, _ = exact.laplacian(g)
+    P = exact.pinv_closed_form(L)
+    b = np.random.default_rng(2).standard_normal(g.n)
+    b -= b.mean()
+    Bt = torch.tensor(b[None, :], dtype=torch.float64, device="cuda")
+    X = torch.empty_like(Bt)
+    rwc.rwc_solve(G.handle, 1, Bt, X, 1e-11)
+    ref = P @ b
+    err = np.abs(X.cpu().numpy()[0] - ref).max() / np.abs(ref).max()
+    assert err < 1e-9, err
 
 
 def test_solver_against_dense_pseudoinverse():

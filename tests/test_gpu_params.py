@@ -1,0 +1,79 @@
+"""GPU parity of the automatic parameters (Section 5) with the oracle: the
+double-sweep diameter and its start vertex exactly; mu = 1 - lambda against
+the dense spectral radius of P_v; t, the tree count and theta against the
+oracle's formulas; full-size graphs against SciPy breadth-first distances."""
+import math
+
+import numpy as np
+import pytest
+
+import paper_2510_20604_gb300 as rwc
+import synth
+from oracle import params as op
+from oracle import wilson as ow
+
+pytestmark = pytest.mark.gpu
+
+GRAPHS = {
+    "path": lambda: synth.path(60),
+    "cycle": lambda: synth.cycle(33),
+    "K7": lambda: synth.complete(7),
+    "star": lambda: synth.star(40, center=3),
+    "grid": lambda: synth.grid2d(20, 23),
+    "ba": lambda: synth.ba(500, 3, seed=1),
+    "rmat12": lambda: synth.rmat(12, 8, seed=2),
+    "weighted": lambda: synth.rgg(600, 10.0, seed=2, sigma=0.5),
+}
+
+
+@pytest.mark.parametrize("gname", list(GRAPHS))
+def test_auto_params_match_oracle(gname):
+    g = GRAPHS[gname]()
+    G = rwc.Graph.from_synth(g)
+    eps = 0.05
+    p = rwc.rwc_auto_params(G.handle, eps)
+    ref = op.auto_params(g, G.root, eps)
+    assert p.diameter == ref["diameter"]
+    assert p.sweep_end == ref["sweep_end"]
+    mu_ref = 1.0 - ref["lambda"]
+    assert p.mu == pytest.approx(mu_ref, rel=1e-6, abs=1e-12)
+    assert p.t == pytest.approx(ref["t"], rel=1e-6)
+    # the tree count and theta follow from t and Delta by the same formulas
+    d = ow.wdeg(g)
+    assert p.trees == op.tree_count(eps, g.n, p.t)
+    assert p.theta == pytest.approx(op.solver_theta(eps, g.n, d.sum() / 2, float(d.max()), p.diameter),
+                                    rel=1e-12)
+
+
+def test_closed_forms():
+    p = rwc.rwc_auto_params(rwc.Graph.from_synth(synth.complete(9)).handle, 0.1)
+    assert p.lambda_ == pytest.approx(7 / 8, abs=1e-9) and p.diameter == 1
+    p = rwc.rwc_auto_params(rwc.Graph.from_synth(synth.cycle(101)).handle, 0.1)
+    assert p.lambda_ == pytest.approx(math.cos(math.pi / 101), abs=1e-9) and p.diameter == 50
+    p = rwc.rwc_auto_params(rwc.Graph.from_synth(synth.star(50, center=0)).handle, 0.1)
+    assert p.lambda_ == pytest.approx(0.0, abs=1e-12) and p.t == 1.0
+
+
+def _scipy_double_sweep(g, v):
+    sp = pytest.importorskip("scipy.sparse")
+    cs = pytest.importorskip("scipy.sparse.csgraph")
+    A = sp.csr_matrix((np.ones(len(g.col)), g.col, g.row_ptr), shape=(g.n, g.n))
+    d1 = cs.shortest_path(A, method="D", unweighted=True, indices=[v])[0]
+    a = int(np.flatnonzero(d1 == d1.max())[0])
+    d2 = cs.shortest_path(A, method="D", unweighted=True, indices=[a])[0]
+    return a, int(d2.max())
+
+
+@pytest.mark.parametrize("which", ["grid1024", "rmat20"])
+def test_full_size_diameter(which):
+    """The benchmark graphs: the 1024^2 grid's diameter is 2046 (exact for
+    grids), R-MAT 20 against SciPy's distances; lambda lies in (0, 1) with
+    the inverse iteration converged."""
+    g = synth.grid2d(1024, 1024) if which == "grid1024" else synth.rmat(20, 16, seed=0)
+    G = rwc.Graph.from_synth(g)
+    p = rwc.rwc_auto_params(G.handle, 0.1)
+    a, delta = _scipy_double_sweep(g, G.root)
+    assert (p.sweep_end, p.diameter) == (a, delta)
+    if which == "grid1024":
+        assert p.diameter == 2046
+    assert 0.0 < p.mu < 1.0 and p.iterations < 30
