@@ -351,3 +351,83 @@ void oracle_rademacher(int32_t k, int64_t n, uint64_t seed, double *Q)
             Q[(int64_t)i * n + u] = (o[0] >> 31) ? -s : s;
         }
 }
+
+/* ------------------------------------------------------------ trap walks */
+
+/* The straightforward estimator of Section 5 (before Wilson's algorithm is
+ * brought in): t_u = (L_v^-1)_uu is the expected number of visits to u of a
+ * random walk started at u and stopped when it meets the trap v (the lemma
+ * connecting t_u with L_v^-1), time 0 included.  For every u != v and every
+ * r < R, one such walk; counts[u] += its visits to u.  Step s of walk (u, r)
+ * moves from x by the RandomNeighbor rule of succ() (multiply-high index,
+ * alias coin for weighted rows) with Philox counter (s, u, r, 0xFFFFFFFE) and
+ * key (seed lo, seed hi).  *steps_out: total steps.  Returns 0, or 1 if a walk
+ * took more than max_steps steps (the walk is cut there and the run flagged). */
+struct tw_task {
+    const graph_t *g;
+    int64_t R, max_steps, steps;
+    int32_t u0, u1;
+    int64_t *counts;
+    int status;
+};
+
+static void *tw_run(void *arg)
+{
+    struct tw_task *t = (struct tw_task *)arg;
+    const graph_t *g = t->g;
+    for (int32_t u = t->u0; u < t->u1; ++u) {
+        if (u == g->root) continue;
+        for (int64_t r = 0; r < t->R; ++r) {
+            int32_t x = u;
+            int64_t c = 0, s = 0;
+            while (x != g->root) {
+                if (x == u) ++c;
+                if (s >= t->max_steps) { t->status = 1; break; }
+                uint32_t ctr[4] = { (uint32_t)s, (uint32_t)u, (uint32_t)r, 0xFFFFFFFEu };
+                uint32_t o[4];
+                oracle_philox4x32_10(ctr, g->key, o);
+                const int64_t b = g->rp[x];
+                const uint32_t deg = (uint32_t)(g->rp[x + 1] - b);
+                uint32_t j = (uint32_t)(((uint64_t)o[0] * (uint64_t)deg) >> 32);
+                if (g->thr != NULL && o[1] >= g->thr[b + j]) j = (uint32_t)g->alias[b + j];
+                x = g->col[b + j];
+                ++s;
+            }
+            t->counts[u] += c;
+            t->steps += s;
+        }
+    }
+    return NULL;
+}
+
+int oracle_trap_walks(int64_t n, const int64_t *rp, const int32_t *col,
+                      const uint32_t *thr, const int32_t *alias, int32_t root,
+                      uint64_t seed, int64_t R, int64_t max_steps, int nthreads,
+                      int64_t *counts, int64_t *steps_out)
+{
+    graph_t g = { n, rp, col, thr, alias, root,
+                  { (uint32_t)seed, (uint32_t)(seed >> 32) }, 0 };
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > n) nthreads = (int)n;
+    struct tw_task *tasks = (struct tw_task *)calloc((size_t)nthreads, sizeof(struct tw_task));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!tasks || !th) { free(tasks); free(th); return -2; }
+    const int64_t step = (n + nthreads - 1) / nthreads;
+    for (int i = 0; i < nthreads; ++i) {
+        tasks[i].g = &g; tasks[i].R = R; tasks[i].max_steps = max_steps; tasks[i].counts = counts;
+        tasks[i].u0 = (int32_t)(i * step < n ? i * step : n);
+        tasks[i].u1 = (int32_t)((i + 1) * step < n ? (i + 1) * step : n);
+    }
+    /* disjoint u ranges: each task writes only its own counts[u] */
+    for (int i = 0; i < nthreads; ++i) pthread_create(&th[i], NULL, tw_run, &tasks[i]);
+    int status = 0;
+    int64_t steps = 0;
+    for (int i = 0; i < nthreads; ++i) {
+        pthread_join(th[i], NULL);
+        if (tasks[i].status) status = tasks[i].status;
+        steps += tasks[i].steps;
+    }
+    if (steps_out) *steps_out = steps;
+    free(tasks); free(th);
+    return status;
+}

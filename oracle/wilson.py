@@ -50,6 +50,9 @@ def lib():
         L.oracle_wdeg.restype = None
         L.oracle_rademacher.argtypes = [_i32, _i64, _u64, _vp]
         L.oracle_rademacher.restype = None
+        L.oracle_trap_walks.argtypes = [_i64, _vp, _vp, _vp, _vp, _i32, _u64, _i64, _i64,
+                                        ctypes.c_int, _vp, _vp]
+        L.oracle_trap_walks.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -138,6 +141,19 @@ class Sampler:
             out["parents"] = par
             out["visits"] = vis
         return out
+
+    def trap_walks(self, R, max_steps=1 << 40, nthreads=None):
+        """Visit counts of the straightforward estimator: for every u != root,
+        R walks from u stopped at the root; counts[u] = visits to u over them
+        (time 0 included).  Returns (counts int64 [n], total steps)."""
+        counts = np.zeros(self.n, np.int64)
+        steps = np.zeros(1, np.int64)
+        st = lib().oracle_trap_walks(self.n, _p(self.rp), _p(self.col), _p(self.thr), _p(self.alias),
+                                     self.root, self.seed, int(R), int(max_steps),
+                                     int(nthreads or cores()), _p(counts), _p(steps))
+        if st != 0:
+            raise RuntimeError(f"oracle_trap_walks status {st}")
+        return counts, int(steps[0])
 
     def tree_with_order(self, tree, order):
         order = np.ascontiguousarray(order, np.int32)
