@@ -309,7 +309,9 @@ def main():
         graphs.append((key, T, g, G, sums))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     opt = rwc.Options(profile=2 if args.diag else 1, block_threads=args.walkers, walker_policy=args.policy)
-    tree_base = rank * 10_000_000
+    from paper_2510_20604_gb300 import shard
+    # weak scaling: every rank samples its own range of global tree ids
+    tree_base = shard.tree_range(rank, world, max(T for _, T in WORKLOADS[args.workload]))[0]
 
     def step(stats_out=None):
         Hs = []

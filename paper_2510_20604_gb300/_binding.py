@@ -103,6 +103,7 @@ def lib():
         "rwc_batch_destroy": ([_vp], _i32),
         "rwc_mre": ([_i64, _vp, _vp, _vp, _vp], _i32),
         "rwc_auto_params": ([_vp, _d, _i32, _d, ctypes.POINTER(Params), _vp], _i32),
+        "rwc_trap_walks": ([_vp, _u64, _i64, _i64, _vp, ctypes.POINTER(_i64), _vp], _i32),
         "rwc_kendall": ([_i64, _vp, _vp, _vp, ctypes.POINTER(_d), _vp], _i32),
     }
     for name, (args, res) in sig.items():
@@ -273,6 +274,16 @@ def rwc_autotune(b, cache_path=None, stream=None):
 
 def rwc_batch_destroy(b):
     _check(lib().rwc_batch_destroy(b))
+
+
+def rwc_trap_walks(g, seed, walks_per_node, sums, max_steps=1 << 32, stream=None) -> int:
+    """Straightforward trap-walk estimator: sums[u] += visits to u of
+    walks_per_node walks from u stopped at the pivot.  Returns total steps."""
+    import torch
+    steps = _i64(0)
+    _check(lib().rwc_trap_walks(g, int(seed), int(walks_per_node), int(max_steps),
+                                _dptr(sums, torch.float64, "sums"), ctypes.byref(steps), _stream(stream)))
+    return steps.value
 
 
 def rwc_auto_params(g, eps, max_iters=0, tol=0.0, stream=None) -> Params:

@@ -4,9 +4,16 @@ backward is the library's hand-written gradient.  All computation happens in
 librwc.so; this module only allocates torch buffers and forwards pointers."""
 from __future__ import annotations
 
+import ctypes
+
 import numpy as np
 
 from . import _binding as B
+
+
+class _Handle(ctypes.c_void_p):
+    """A C handle that keeps the Python object owning it alive: passing
+    ``Graph(...).handle`` straight to a call cannot free the graph first."""
 
 
 class Graph:
@@ -17,9 +24,17 @@ class Graph:
         col_idx = np.ascontiguousarray(col_idx, np.int32)
         self.row_ptr, self.col_idx = row_ptr, col_idx
         self.w = None if w is None else np.ascontiguousarray(w, np.float32)
-        self.handle = B.rwc_graph_create(len(row_ptr) - 1, int(row_ptr[-1]), row_ptr, col_idx,
-                                         self.w, root, flags)
-        self.info = B.rwc_graph_info(self.handle)
+        self._ptr = B.rwc_graph_create(len(row_ptr) - 1, int(row_ptr[-1]), row_ptr, col_idx,
+                                       self.w, root, flags)
+        self.info = B.rwc_graph_info(self._ptr)
+
+    @property
+    def handle(self):
+        if not self._ptr:
+            raise B.RWCError(1, "graph handle used after close()")
+        h = _Handle(self._ptr)
+        h.owner = self
+        return h
 
     @classmethod
     def from_synth(cls, g, root=-1, flags=0):
@@ -31,9 +46,9 @@ class Graph:
     vol = property(lambda self: self.info.vol)
 
     def close(self):
-        if getattr(self, "handle", None):
-            B.rwc_graph_destroy(self.handle)
-            self.handle = None
+        if getattr(self, "_ptr", None):
+            B.rwc_graph_destroy(self._ptr)
+            self._ptr = None
 
     def __del__(self):
         try:
@@ -92,8 +107,16 @@ class Batch:
         self.row_ptr = np.concatenate(rps)
         self.col = np.concatenate(cols)
         w = None if any(x is None for x in ws) else np.concatenate(ws).astype(np.float32)
-        self.handle = B.rwc_batch_create(self.G, self.offsets, self.row_ptr, self.col, w)
+        self._ptr = B.rwc_batch_create(self.G, self.offsets, self.row_ptr, self.col, w)
         self.N = int(self.offsets[-1])
+
+    @property
+    def handle(self):
+        if not self._ptr:
+            raise B.RWCError(1, "batch handle used after close()")
+        h = _Handle(self._ptr)
+        h.owner = self
+        return h
 
     def roots(self):
         return B.rwc_batch_roots(self.handle, self.G)
@@ -111,9 +134,9 @@ class Batch:
         B.rwc_autotune(self.handle, cache_path, stream)
 
     def close(self):
-        if getattr(self, "handle", None):
-            B.rwc_batch_destroy(self.handle)
-            self.handle = None
+        if getattr(self, "_ptr", None):
+            B.rwc_batch_destroy(self._ptr)
+            self._ptr = None
 
     def __del__(self):
         try:

@@ -52,8 +52,12 @@ __device__ __forceinline__ void row_range(const DevGraph &g, int64_t u, int64_t 
 }
 
 // Level-synchronous BFS from src: dist[u] = hops, out[0] = eccentricity of
-// src.  flag[L & 1] records whether level L reached a new vertex; the flag of
-// the next level is cleared before the barrier that ends this level.
+// src.  flag[L % 3] records whether level L reached a new vertex and is read
+// by every thread after the barrier that ends level L.  The flag of level
+// L + 1 is cleared at the start of level L: its slot was last read after the
+// barrier of level L - 2, and every thread has passed the barrier of level
+// L - 1 since (two slots would let a fast thread clear a flag that a slow one
+// has yet to read).
 template <bool OFF64>
 __global__ void __launch_bounds__(PT) bfs_coop(DevGraph g, int32_t src, int32_t *dist, int *flag,
                                                 int *out) {
@@ -61,11 +65,11 @@ __global__ void __launch_bounds__(PT) bfs_coop(DevGraph g, int32_t src, int32_t 
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
     for (int64_t u = tid; u < g.n; u += nthr) dist[u] = (u == src) ? 0 : -1;
-    if (tid == 0) { flag[0] = 0; flag[1] = 0; }
+    if (tid == 0) { flag[0] = 0; flag[1] = 0; flag[2] = 0; }
     grid.sync();
     int L = 0;
     for (; L < g.n; ++L) {
-        if (tid == 0) flag[(L + 1) & 1] = 0;
+        if (tid == 0) flag[(L + 1) % 3] = 0;
         bool any = false;
         for (int64_t u = tid; u < g.n; u += nthr) {
             if (ld_gpu(dist + u) != L) continue;
@@ -76,9 +80,9 @@ __global__ void __launch_bounds__(PT) bfs_coop(DevGraph g, int32_t src, int32_t 
                 if (ld_gpu(dist + c) < 0 && atomicCAS(dist + c, -1, L + 1) == -1) any = true;
             }
         }
-        if (any) atomicOr(flag + (L & 1), 1);
+        if (any) atomicOr(flag + (L % 3), 1);
         grid.sync();
-        if (ld_gpu(flag + (L & 1)) == 0) break;
+        if (ld_gpu(flag + (L % 3)) == 0) break;
     }
     if (tid == 0) out[0] = L;
 }
@@ -188,7 +192,7 @@ extern "C" rwc_status rwc_auto_params(rwc_graph_t *G, double eps, int32_t max_it
     int32_t *dist = (int32_t *)buf.p;
     double *x = (double *)((char *)buf.p + dist_b), *c = x + n, *z = c + n;
     char *sc = (char *)(z + n);
-    int *flag = (int *)sc;            // [2]
+    int *flag = (int *)sc;            // [3]
     int *iout = (int *)(sc + 16);     // [0] eccentricity, [1] farthest vertex
     double *acc = (double *)(sc + 64);
     int64_t *h = G->host_scalars;

@@ -46,11 +46,14 @@ def test_auto_params_match_oracle(gname):
 
 
 def test_closed_forms():
-    p = rwc.rwc_auto_params(rwc.Graph.from_synth(synth.complete(9)).handle, 0.1)
+    G = rwc.Graph.from_synth(synth.complete(9))
+    p = rwc.rwc_auto_params(G.handle, 0.1)
     assert p.lambda_ == pytest.approx(7 / 8, abs=1e-9) and p.diameter == 1
-    p = rwc.rwc_auto_params(rwc.Graph.from_synth(synth.cycle(101)).handle, 0.1)
+    G = rwc.Graph.from_synth(synth.cycle(101))
+    p = rwc.rwc_auto_params(G.handle, 0.1)
     assert p.lambda_ == pytest.approx(math.cos(math.pi / 101), abs=1e-9) and p.diameter == 50
-    p = rwc.rwc_auto_params(rwc.Graph.from_synth(synth.star(50, center=0)).handle, 0.1)
+    G = rwc.Graph.from_synth(synth.star(50, center=0))
+    p = rwc.rwc_auto_params(G.handle, 0.1)
     assert p.lambda_ == pytest.approx(0.0, abs=1e-12) and p.t == 1.0
 
 
