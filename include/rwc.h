@@ -124,9 +124,10 @@ typedef struct {
     double phase_ms[RWC_NPHASE];
     int64_t phase_launches[RWC_NPHASE];
     int64_t phase_units[RWC_NPHASE];
-    /* diagnostics; WALKER mode: loop iterations summed over all walkers in
-     * the states idle, walk, pop, release, settle, wait-for-yield,
-     * wait-after-yield (or wait for an earlier walk's vertex) */
+    /* diagnostics; WALKER mode with profile = 2: [0..6] loop iterations
+     * summed over all walkers in the states idle, walk, pop, release, settle,
+     * wait-for-yield, wait-after-yield (or wait for an earlier walk's vertex);
+     * [7] loop iterations summed over warps */
     int64_t diag[8];
 } rwc_stats_t;
 
@@ -308,6 +309,24 @@ rwc_status rwc_batch_roots(const rwc_batch_t *b, int32_t *host_roots);
  * the device; results are cached in cache_path (JSON, may be NULL). */
 rwc_status rwc_autotune(rwc_batch_t *b, const char *cache_path, rwc_stream_t stream);
 rwc_status rwc_batch_destroy(rwc_batch_t *b);
+
+/*
+ * The straightforward estimator of Section 5 (the one Wilson's algorithm
+ * improves on), for comparison: t_u = (NL_v^-1)_uu is the expected number of
+ * visits to u of a random walk from u stopped when it meets the pivot v
+ * (time 0 included).  For every u != v and r < walks_per_node, one such walk;
+ * sums[u] += its visits to u, so that sums / walks_per_node estimates the same
+ * t as the tree sampler's sums / num_trees (and can be passed to rwc_estimate
+ * with num_trees = walks_per_node).  Step s of walk (u, r) moves by the tree
+ * sampler's RandomNeighbor rule with Philox counter (s, u, r, 0xFFFFFFFE) and
+ * key = seed.  walks_per_node in [0, 2^32], max_steps in [1, 2^32]: a walk
+ * longer than max_steps ends the call with RWC_ERR_NOT_CONVERGED.
+ * sums: FP64 [n] device, accumulated.  host_steps: NULL or total steps taken.
+ * Synchronises stream.
+ */
+rwc_status rwc_trap_walks(rwc_graph_t *g, uint64_t seed, int64_t walks_per_node,
+                          int64_t max_steps, double *sums, int64_t *host_steps,
+                          rwc_stream_t stream);
 
 /*
  * Automatic parameters (Section 5, "The Sampling Algorithm": the sample size
