@@ -103,6 +103,11 @@ def make_graph(key):
     raise KeyError(key)
 
 
+def graph_flags(key, rwc):
+    """R-MAT 24 is stored with int64 arc offsets (its configuration asks for them)."""
+    return rwc.GRAPH_INT64_OFFSETS if key == "rmat24" else 0
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -304,7 +309,7 @@ def main():
     graphs = []
     for key, T in WORKLOADS[args.workload]:
         g = make_graph(key)
-        G = rwc.Graph.from_synth(g)
+        G = rwc.Graph.from_synth(g, flags=graph_flags(key, rwc))
         sums = torch.zeros(g.n, dtype=torch.float64, device=dev)
         graphs.append((key, T, g, G, sums))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -437,7 +442,8 @@ def main():
         t0 = time.perf_counter()
         for _ in range(e_steps):
             for key, T, g, rp, ci, ww, Hh in pinned:
-                h = rwc.rwc_graph_create(g.n, g.nnz, rp.numpy(), ci.numpy(), None if ww is None else ww.numpy())
+                h = rwc.rwc_graph_create(g.n, g.nnz, rp.numpy(), ci.numpy(), None if ww is None else ww.numpy(),
+                                         flags=graph_flags(key, rwc))
                 try:
                     s = torch.zeros(g.n, dtype=torch.float64, device=dev)
                     rwc.rwc_sample_trees(h, 1, tree_base, T, s)

@@ -218,6 +218,11 @@ __global__ void __maxnreg__(RWC_WALKER_MAXNREG) w_trees(DevGraph g, WState s, in
             const bool err = vread(&sh_err) != 0;
             if (__any_sync(0xffffffffu, err)) break;
             if (__all_sync(0xffffffffu, state == S_DONE)) break;
+            // a warp whose walkers all wait gives its issue slots to the others
+            if (__all_sync(0xffffffffu, state == S_DONE || state == S_WAITV || state == S_WAITK ||
+                                            state == S_WAITH))
+                __nanosleep(200);
+            if (DIAG && (threadIdx.x & 31) == 0) ++it_state[S_DONE];   // warp iterations
             if (state == S_DONE) continue;
             if (DIAG) ++it_state[state];
             do {
@@ -457,7 +462,10 @@ __global__ void __maxnreg__(RWC_WALKER_MAXNREG) w_trees(DevGraph g, WState s, in
     if (DIAG && pops) atomicAdd(&s.ctr[2], pops);
     if (DIAG && s.diag)
         for (int i = 0; i < 8; ++i) {
-            const unsigned long long v = it_state[i] + (i == S_WAITV ? it_state[S_WAITH] : 0ull);
+            // [0..6] lane iterations per state (wait-for-owner counted with
+            // wait-after-yield), [7] warp iterations
+            const unsigned long long v = i == 7 ? it_state[S_DONE]
+                                       : it_state[i] + (i == S_WAITV ? it_state[S_WAITH] : 0ull);
             if (v) atomicAdd(&s.diag[i], v);
         }
 }
