@@ -68,7 +68,16 @@ def bytes_per_unit(phase, mode, weighted, off64):
 # dominant kernel, from one ncu capture per workload; valid only for the kernel
 # source it was measured on (SHA-256 of the .cu file), else reported as null.
 TRAFFIC = {
-    # (workload, kernel): (bytes per launch, source file, sha256 of the source)
+    # (workload, kernel): (bytes per launch, source file, sha256 of the source);
+    # captured with --metrics dram__bytes_read.sum,dram__bytes_write.sum (one
+    # pass, the full-size launches of the benchmark's own command)
+    ("grid1024+rmat20", "w_trees"): (  # mean of the grid's and R-MAT 20's launch
+        (6769484750336 + 2453061375232 + 652894970112 + 93141526016) / 2, "walker.cu",
+        "549826a931c3cdb17335c02c44311b8a0ada74a6a22a09f6779e093f0230891b"),
+    ("grid1024", "w_trees"): (6769484750336 + 2453061375232, "walker.cu",
+                              "549826a931c3cdb17335c02c44311b8a0ada74a6a22a09f6779e093f0230891b"),
+    ("rmat20", "w_trees"): (652894970112 + 93141526016, "walker.cu",
+                            "549826a931c3cdb17335c02c44311b8a0ada74a6a22a09f6779e093f0230891b"),
 }
 
 
@@ -402,8 +411,12 @@ def main():
     per_launch_s = phase_ms[dom] / 1000.0 / nl
     achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
     kname = KERNEL_NAMES.get(dom_mode, {}).get(dom, dom)
+    traffic = traffic_for(args.workload, kname)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": traffic_for(args.workload, kname),
+                "frac": achieved / hbm_peak, "traffic": traffic,
+                # DRAM bytes actually moved (ncu, per launch) over the live launch time
+                "dram_gbs": traffic / per_launch_s / 1e9 if traffic and per_launch_s > 0 else None,
+                "dram_frac": traffic / per_launch_s / 1e9 / hbm_peak if traffic and per_launch_s > 0 else None,
                 "algorithmic_bytes_per_launch": per_launch_bytes,
                 "kernel": KERNEL_NAMES.get(dom_mode, {}).get(dom, dom),
                 "unit_bytes": bytes_per_unit(dom, dom_mode, False, False),
