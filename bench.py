@@ -376,10 +376,9 @@ def main():
     for (key, T, g, G, sums), H in zip(graphs, Hs):
         s = sums.cpu().numpy()
         h = H.cpu().numpy()
-        d = np.diff(g.row_ptr).astype(np.float64) if g.w is None else None
-        if d is None:
-            from oracle import wilson as ow  # weighted degrees only for reporting
-            d = ow.wdeg(g)
+        # (weighted) degrees for the report: row sums of the arc weights
+        d = (np.diff(g.row_ptr).astype(np.float64) if g.w is None
+             else np.add.reduceat(g.w.astype(np.float64), g.row_ptr[:-1]))
         pi = d / d.sum()
         t = s / T
         se = np.sqrt(np.maximum(t * (t - 1.0), 0.0) / T) / pi
