@@ -66,30 +66,36 @@ def bytes_per_unit(phase, mode, weighted, off64):
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # dominant kernel, from one ncu capture per workload; valid only for the kernel
-# source it was measured on (SHA-256 of the .cu file), else reported as null.
+# source it was measured on (code_hash of the .cu file), else reported as null.
 TRAFFIC = {
     # (workload, kernel): (bytes per launch, source file, sha256 of the source);
     # captured with --metrics dram__bytes_read.sum,dram__bytes_write.sum (one
     # pass, the full-size launches of the benchmark's own command)
-    ("grid1024+rmat20", "w_trees"): (  # mean of the grid's and R-MAT 20's launch
-        (6769484750336 + 2453061375232 + 652894970112 + 93141526016) / 2, "walker.cu",
-        "549826a931c3cdb17335c02c44311b8a0ada74a6a22a09f6779e093f0230891b"),
-    ("grid1024", "w_trees"): (6769484750336 + 2453061375232, "walker.cu",
-                              "549826a931c3cdb17335c02c44311b8a0ada74a6a22a09f6779e093f0230891b"),
-    ("rmat20", "w_trees"): (652894970112 + 93141526016, "walker.cu",
-                            "549826a931c3cdb17335c02c44311b8a0ada74a6a22a09f6779e093f0230891b"),
+    ("grid1024+rmat20", "w_trees"): (6545542676864, "walker.cu",  # mean of the two launches
+                                     "ad13d7d3a099b5a5ca93403edecb60ebee89f04ac9ed351061b6a95d5b58678b"),
+    ("grid1024", "w_trees"): (12342229051904, "walker.cu", "ad13d7d3a099b5a5ca93403edecb60ebee89f04ac9ed351061b6a95d5b58678b"),
+    ("rmat20", "w_trees"): (748856301824, "walker.cu", "ad13d7d3a099b5a5ca93403edecb60ebee89f04ac9ed351061b6a95d5b58678b"),
 }
 
 
-def traffic_for(workload, kernel):
+def code_hash(path):
+    """SHA-256 of a source file's code: every line except blank lines and
+    lines that hold only a // comment (so that rewording a comment keeps a
+    measurement, while any change to the code voids it)."""
     import hashlib
+    lines = [ln.rstrip() for ln in open(path, encoding="utf-8")]
+    code = [ln for ln in lines if ln.strip() and not ln.strip().startswith("//")]
+    return hashlib.sha256("\n".join(code).encode()).hexdigest()
+
+
+def traffic_for(workload, kernel):
     ent = TRAFFIC.get((workload, kernel))
     if not ent:
         return None
     nbytes, src, sha = ent
     path = os.path.join(ROOT, "paper_2510_20604_gb300", "csrc", src)
     try:
-        cur = hashlib.sha256(open(path, "rb").read()).hexdigest()
+        cur = code_hash(path)
     except OSError:
         return None
     return nbytes if cur == sha else None
@@ -283,7 +289,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=20.0)
     ap.add_argument("--walkers", type=int, default=0, help="walkers per tree (0 = auto)")
-    ap.add_argument("--policy", type=int, default=0, help="walker conflict policy (0 auto, 1 yield, 2 wait)")
+    ap.add_argument("--policy", type=int, default=0, help="walker conflict policy (0 default = 3, 1 yield and wait, 2 wait, 3 yield and take a fresh start)")
     ap.add_argument("--diag", action="store_true", help="count walker loop iterations per state (slower)")
     args = ap.parse_args()
     if args.trees:

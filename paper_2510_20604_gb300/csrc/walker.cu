@@ -20,10 +20,12 @@
 //   yield   if the head points into another walker's path, the walker whose
 //           start comes later in the processing order releases its path
 //           (owners set to FREE, cached p kept) and requeues its start.
-// A walker that yielded takes no new start until the walker it yielded to
-// has changed state (every walker publishes a version counter), so the
-// earlier walk always gets the contested vertex first.  The earliest active
-// walk never yields, so the block always makes progress.
+// A walker that yielded takes no requeued start until the walker it yielded
+// to has changed state (every walker publishes a version counter), so the
+// earlier walk gets the contested vertex first; by default it takes a fresh
+// start at once while fresh starts remain, since those lie elsewhere in the
+// graph.  The earliest active walk never yields, so the block always makes
+// progress.
 // Waits are bounded; on exhaustion the block records an error and stops.
 #include <algorithm>
 #include <cstring>
@@ -604,7 +606,7 @@ rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, 
             if (st) st->block_threads = Wc;
             ::rwc::count_launches(1);
             kern<<<(unsigned)blocks, Wc, smem, stream>>>(g, ws, Bc, (uint32_t)(tree0 + c0), k0, k1, max_wait,
-                                                         o.walker_policy == 2 ? 1 : o.walker_policy == 3 ? 2 : 0);
+                                                         o.walker_policy == 2 ? 1 : o.walker_policy == 1 ? 0 : 2);
         });
         RWC_TRY(status);
         if (prof) cudaEventRecord(ev[2], stream);

@@ -80,3 +80,21 @@ def test_missing_library_fails_loudly(monkeypatch):
     monkeypatch.setattr(_binding, "lib_path", "/nonexistent/librwc.so")
     with pytest.raises(rwc.RWCError):
         _binding.lib()
+
+
+def test_evaluation_and_walk_entry_points_reject_bad_arguments():
+    """Argument checks of rwc_mre, rwc_kendall, rwc_trap_walks and
+    rwc_auto_params happen on the host, before any device work."""
+    L = rwc.lib()
+    d = ctypes.c_double(0.0)
+    # rwc_mre: n >= 1 and non-NULL pointers
+    assert L.rwc_mre(0, 8, 8, 8, None) == 1
+    assert L.rwc_mre(5, None, 8, 8, None) == 1
+    # rwc_kendall: 0 <= n <= 2^26, out pointer required
+    assert L.rwc_kendall(-1, 8, 8, 8, None, None) == 1
+    assert L.rwc_kendall((1 << 26) + 1, 8, 8, 8, None, None) == 1
+    assert L.rwc_kendall(10, 8, 8, None, None, None) == 1
+    assert "2^26" in rwc.rwc_last_error() or "NULL" in rwc.rwc_last_error()
+    # rwc_trap_walks / rwc_auto_params: a graph is required
+    assert L.rwc_trap_walks(None, 1, 4, 100, 8, None, None) == 1
+    assert L.rwc_auto_params(None, 0.1, 0, 0.0, None, None) == 1

@@ -59,3 +59,31 @@ def test_mre_matches_oracle(n):
     assert got == pytest.approx(ev.mre(H, He), rel=1e-12, abs=0)
     # deterministic reduction order
     assert float(rwc.rwc_mre(_cuda(H), _cuda(He)).item()) == got
+
+
+def test_tree_count_sweep_small_config():
+    """The accuracy sweep of Section 6 on the small configuration (BA n = 2000
+    + path, exact H from the dense oracle), as curve shapes: with 4x the
+    trees the device MRE halves (1/sqrt(l), within 25%) and the device
+    Kendall distance to the exact ranking rises towards 1; both device
+    measures equal the oracle's on the same vectors."""
+    import synth
+    from oracle import exact
+    g = synth.ba(2000, 3, seed=0)
+    G = rwc.Graph.from_synth(g)
+    Hx = exact.rwc_pinv(g)
+    Hx_d = _cuda(Hx)
+    mres, taus = [], []
+    for T in (250, 1000, 4000):
+        sums, _, _, _ = G.sample(T, seed=1)
+        H = G.estimate(sums, T)
+        m = float(rwc.rwc_mre(Hx_d, H).item())
+        tau, diff = rwc.rwc_kendall(H, Hx_d)
+        Hn = H.cpu().numpy()
+        assert m == pytest.approx(ev.mre(Hx, Hn), rel=1e-12, abs=0)
+        assert diff == ev.kendall_counts(Hn, Hx)
+        mres.append(m)
+        taus.append(tau)
+    for a, b in zip(mres, mres[1:]):
+        assert 0.5 * 0.75 < b / a < 0.5 * 1.25, mres
+    assert taus[0] < taus[1] < taus[2] < 1.0, taus
