@@ -51,7 +51,7 @@ KERNEL_NAMES = {1: {"init": "g_init", "walk": "g_walk", "pop": "g_pop", "accum":
 
 
 def bytes_per_unit(phase, mode, weighted, off64):
-    """Algorithmic bytes per work unit of each sampler phase (see DESIGN.md).
+    """Algorithmic bytes per work unit of each sampler phase.
     mode: 1 round-based (GLOBAL), 2 shared memory, 3 concurrent walkers."""
     row = 16 if off64 else 8
     arc = 16 if weighted else 4
@@ -71,10 +71,10 @@ TRAFFIC = {
     # (workload, kernel): (bytes per launch, source file, sha256 of the source);
     # captured with --metrics dram__bytes_read.sum,dram__bytes_write.sum (one
     # pass, the full-size launches of the benchmark's own command)
-    ("grid1024+rmat20", "w_trees"): (6545542676864, "walker.cu",  # mean of the two launches
-                                     "ad13d7d3a099b5a5ca93403edecb60ebee89f04ac9ed351061b6a95d5b58678b"),
-    ("grid1024", "w_trees"): (12342229051904, "walker.cu", "ad13d7d3a099b5a5ca93403edecb60ebee89f04ac9ed351061b6a95d5b58678b"),
-    ("rmat20", "w_trees"): (748856301824, "walker.cu", "ad13d7d3a099b5a5ca93403edecb60ebee89f04ac9ed351061b6a95d5b58678b"),
+    ("grid1024+rmat20", "w_trees"): (6549618983296, "walker.cu",  # mean of the two launches
+                                     "f49c11e1e8726513496a7564ee7f4d0c5e37783339f7197f1f8cb05e520cebd1"),
+    ("grid1024", "w_trees"): (12348197538560, "walker.cu", "f49c11e1e8726513496a7564ee7f4d0c5e37783339f7197f1f8cb05e520cebd1"),
+    ("rmat20", "w_trees"): (751040428032, "walker.cu", "f49c11e1e8726513496a7564ee7f4d0c5e37783339f7197f1f8cb05e520cebd1"),
 }
 
 
@@ -289,7 +289,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=20.0)
     ap.add_argument("--walkers", type=int, default=0, help="walkers per tree (0 = auto)")
-    ap.add_argument("--policy", type=int, default=0, help="walker conflict policy (0 default = 3, 1 yield and wait, 2 wait, 3 yield and take a fresh start)")
+    ap.add_argument("--policy", type=int, default=0, help="walker conflict policy (0 default: 3 up to 64 walkers per tree, else 1; 1 yield and wait, 2 wait, 3 yield and take a fresh start)")
     ap.add_argument("--diag", action="store_true", help="count walker loop iterations per state (slower)")
     args = ap.parse_args()
     if args.trees:

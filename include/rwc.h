@@ -88,7 +88,8 @@ typedef struct {
                                  2 = also count walker loop iterations per state
                                  (rwc_stats_t.diag; slower kernel variant) */
     int32_t walker_policy;    /* WALKER mode, when a walk runs into an earlier
-                                 walk's path: 0 = default (3), 1 = yield (free the
+                                 walk's path: 0 = default (3 when a tree has at
+                                 most 64 walkers, else 1), 1 = yield (free the
                                  path, requeue, wait for the earlier walk to move
                                  on), 2 = wait (keep the path until the vertex
                                  changes owner), 3 = yield and take a fresh start

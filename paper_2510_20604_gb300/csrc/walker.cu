@@ -22,9 +22,9 @@
 //           (owners set to FREE, cached p kept) and requeues its start.
 // A walker that yielded takes no requeued start until the walker it yielded
 // to has changed state (every walker publishes a version counter), so the
-// earlier walk gets the contested vertex first; by default it takes a fresh
-// start at once while fresh starts remain, since those lie elsewhere in the
-// graph.  The earliest active walk never yields, so the block always makes
+// earlier walk gets the contested vertex first; with few walkers per tree it
+// takes a fresh start at once while fresh starts remain (by default), since
+// those lie elsewhere in the graph.  The earliest active walk never yields, so the block always makes
 // progress.
 // Waits are bounded; on exhaustion the block records an error and stops.
 #include <algorithm>
@@ -605,8 +605,12 @@ rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, 
             const int64_t blocks = std::min<int64_t>(Bc, (int64_t)sms * per_sm);
             if (st) st->block_threads = Wc;
             ::rwc::count_launches(1);
+            // default conflict policy: with few walkers per tree (many trees)
+            // a walker that yielded takes a fresh start at once (3), with many
+            // it waits for the winner (1), which keeps collisions down
+            const int pol = o.walker_policy != 0 ? o.walker_policy : (Wc <= 64 ? 3 : 1);
             kern<<<(unsigned)blocks, Wc, smem, stream>>>(g, ws, Bc, (uint32_t)(tree0 + c0), k0, k1, max_wait,
-                                                         o.walker_policy == 2 ? 1 : o.walker_policy == 1 ? 0 : 2);
+                                                         pol == 2 ? 1 : pol == 3 ? 2 : 0);
         });
         RWC_TRY(status);
         if (prof) cudaEventRecord(ev[2], stream);
