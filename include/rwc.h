@@ -19,8 +19,10 @@
  *    owns and frees in the matching *_destroy call.
  *  - stream is a cudaStream_t (NULL = the legacy default stream).  Work is
  *    enqueued on it; entry points that must inspect device results
- *    (rwc_sample_trees, rwc_estimate, rwc_grad, rwc_batch_sample) synchronise
- *    that stream before returning, so their outputs are ready on return.
+ *    (rwc_sample_trees, rwc_sample_trees_noalloc, rwc_estimate, rwc_solve,
+ *    rwc_grad, rwc_batch_sample, rwc_trap_walks, rwc_auto_params) synchronise
+ *    that stream before returning, so their outputs are ready on return and
+ *    device-side errors come back as their status.
  *  - Graphs are undirected, given as CSR with both arc directions: row u
  *    lists the neighbours of u.  Vertex ids are int32; n >= 2.
  *  - All functions are safe to call from several host threads on distinct
