@@ -73,3 +73,24 @@ def estimate(d, v, sums, ntrees, z):
     t = np.asarray(sums, np.float64) / float(ntrees)
     y = y_from_z(d, z)
     return recover_vec(d, v, t, y), y
+
+
+def predicted_mre(d: np.ndarray, v: int, sums: np.ndarray, T: int, H: np.ndarray) -> float:
+    """Mean relative error to expect from T trees (the variance law of the
+    visit counts): visits_u per tree are geometric with mean t_u, so t~_u =
+    sums_u / T has variance t_u (t_u - 1) / T; H~_u = (t~_u - ...) / pi_u
+    carries that error divided by pi_u (H~_v carries none), and a normal error
+    of standard deviation s has mean absolute value sqrt(2/pi) s.  t_u is
+    replaced by its estimate.  MRE = mean over all n vertices of
+    sqrt(2/pi) se_u / |H_u|."""
+    d = np.asarray(d, np.float64)
+    pi = d / d.sum()
+    t = np.asarray(sums, np.float64) / T
+    se = np.sqrt(np.maximum(t * (t - 1.0), 0.0) / T) / pi
+    se[v] = 0.0
+    return float(np.sqrt(2.0 / np.pi) * np.mean(se / np.abs(H)))
+
+
+def trees_for(mre: float, T: int, target: float) -> int:
+    """Trees needed for the target MRE (the error falls as 1/sqrt(T))."""
+    return int(np.ceil(T * (mre / target) ** 2))

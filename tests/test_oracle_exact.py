@@ -104,3 +104,26 @@ def test_estimator_converges_on_small_ba():
     mre = np.mean(np.abs(Hest - H) / H)
     pred = np.sqrt(2 / np.pi) * np.mean(sd / H)
     assert 0.5 * pred < mre < 1.5 * pred
+
+
+def test_predicted_mre_matches_measured_error():
+    """The variance-law prediction against the error the oracle's own trees
+    actually make against the exact H (BA n = 2000 + path, the small
+    configuration), at two tree counts; and the 1/sqrt(T) rule for the trees
+    needed."""
+    from oracle import apprwc
+    from oracle import wilson as ow
+    g = synth.ba(2000, 3, seed=0)
+    s = ow.Sampler(g, seed=1)
+    v = s.root
+    d = ow.wdeg(g)
+    Hx = exact.rwc_pinv(g)
+    y = exact.pivot_column(g, v)
+    for T in (400, 1600):
+        sums = s.sample(0, T, nthreads=ow.cores())["sums"]
+        H = apprwc.recover_vec(d, v, sums / T, y)
+        measured = float(np.mean(np.abs(H - Hx) / Hx))
+        pred = apprwc.predicted_mre(d, v, sums, T, H)
+        assert 0.75 * pred < measured < 1.25 * pred, (T, measured, pred)
+    assert apprwc.trees_for(0.02, 1000, 0.01) == 4000
+    assert apprwc.trees_for(0.01, 1000, 0.01) == 1000
