@@ -21,7 +21,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys
@@ -377,21 +376,13 @@ def main():
     total_T = sum(T for _, T in WORKLOADS[args.workload])
     value = world * total_T / (ms / 1000.0)
 
-    # accuracy: predicted MRE from the geometric variance of visit counts
+    # accuracy: predicted MRE from the variance law of the visit counts (the
+    # library's stopping rule) and the trees it needs for 1%
     acc = {}
     for (key, T, g, G, sums), H in zip(graphs, Hs):
-        s = sums.cpu().numpy()
-        h = H.cpu().numpy()
-        # (weighted) degrees for the report: row sums of the arc weights
-        d = (np.diff(g.row_ptr).astype(np.float64) if g.w is None
-             else np.add.reduceat(g.w.astype(np.float64), g.row_ptr[:-1]))
-        pi = d / d.sum()
-        t = s / T
-        se = np.sqrt(np.maximum(t * (t - 1.0), 0.0) / T) / pi
-        mre = float(math.sqrt(2 / math.pi) * np.mean(se / h))
-        T1 = int(math.ceil(T * (mre / 0.01) ** 2))
-        acc[key] = {"mre_pred": mre, "trees_for_1pct": T1, "n": g.n,
-                    "draws_per_tree": float(s.sum() / T)}
+        mre, T1 = rwc.rwc_predict_mre(G.handle, sums, T, H, target=0.01)
+        acc[key] = {"mre_pred": mre, "trees_for_1pct": int(T1), "n": g.n,
+                    "draws_per_tree": float(sums.sum().item() / T)}
 
     # per-kernel roofline from the profiled phases (timed region only)
     phase_ms = {p: 0.0 for p in PHASE_NAMES}

@@ -20,7 +20,8 @@
  *  - stream is a cudaStream_t (NULL = the legacy default stream).  Work is
  *    enqueued on it; entry points that must inspect device results
  *    (rwc_sample_trees, rwc_sample_trees_noalloc, rwc_estimate, rwc_solve,
- *    rwc_grad, rwc_batch_sample, rwc_trap_walks, rwc_auto_params) synchronise
+ *    rwc_grad, rwc_batch_sample, rwc_trap_walks, rwc_auto_params,
+ *    rwc_predict_mre) synchronise
  *    that stream before returning, so their outputs are ready on return and
  *    device-side errors come back as their status.
  *  - Graphs are undirected, given as CSR with both arc directions: row u
@@ -377,6 +378,22 @@ rwc_status rwc_auto_params(rwc_graph_t *g, double eps, int32_t max_iters, double
  */
 rwc_status rwc_mre(int64_t n, const double *H, const double *H_est, double *out,
                    rwc_stream_t stream);
+
+/*
+ * rwc_predict_mre: the stopping rule of the variance law of the visit counts.
+ * Per tree, visits_u is geometric with mean t_u, so t~_u = sums_u / T has
+ * variance t_u (t_u - 1) / T, and H~_u = (t~_u - ...) / pi_u carries that
+ * error over pi_u (H~_v carries none); a normal error of standard deviation s
+ * has mean absolute value sqrt(2/pi) s.  With t_u replaced by its estimate:
+ *   mre   = (1/n) sum_{u != v} sqrt(2/pi) sqrt(t~_u (t~_u - 1) / T) / (pi_u |H_u|)
+ *   trees = ceil(T (mre / target)^2), the trees for a target error
+ * sums: FP64 [n] device (the visit totals of num_trees trees); H: FP64 [n]
+ * device (rwc_estimate's output).  host_mre: host double; host_trees: NULL or
+ * host int64, written when target > 0.  Synchronises stream.
+ */
+rwc_status rwc_predict_mre(rwc_graph_t *g, const double *sums, int64_t num_trees, const double *H,
+                           double target, double *host_mre, int64_t *host_trees,
+                           rwc_stream_t stream);
 
 /*
  * rwc_kendall: Kendall distance of the rankings given by a and b,

@@ -104,6 +104,7 @@ def lib():
         "rwc_mre": ([_i64, _vp, _vp, _vp, _vp], _i32),
         "rwc_auto_params": ([_vp, _d, _i32, _d, ctypes.POINTER(Params), _vp], _i32),
         "rwc_trap_walks": ([_vp, _u64, _i64, _i64, _vp, ctypes.POINTER(_i64), _vp], _i32),
+        "rwc_predict_mre": ([_vp, _vp, _i64, _vp, _d, ctypes.POINTER(_d), ctypes.POINTER(_i64), _vp], _i32),
         "rwc_kendall": ([_i64, _vp, _vp, _vp, ctypes.POINTER(_d), _vp], _i32),
     }
     for name, (args, res) in sig.items():
@@ -284,6 +285,18 @@ def rwc_trap_walks(g, seed, walks_per_node, sums, max_steps=1 << 32, stream=None
     _check(lib().rwc_trap_walks(g, int(seed), int(walks_per_node), int(max_steps),
                                 _dptr(sums, torch.float64, "sums"), ctypes.byref(steps), _stream(stream)))
     return steps.value
+
+
+def rwc_predict_mre(g, sums, num_trees, H, target=0.01, stream=None):
+    """(predicted MRE of the estimate H from num_trees trees, trees needed for
+    the target MRE) by the variance law of the visit counts."""
+    import torch
+    m = _d(0.0)
+    t = _i64(0)
+    _check(lib().rwc_predict_mre(g, _dptr(sums, torch.float64, "sums"), int(num_trees),
+                                 _dptr(H, torch.float64, "H"), float(target), ctypes.byref(m),
+                                 ctypes.byref(t), _stream(stream)))
+    return m.value, t.value
 
 
 def rwc_auto_params(g, eps, max_iters=0, tol=0.0, stream=None) -> Params:

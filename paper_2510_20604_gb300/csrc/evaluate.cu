@@ -13,6 +13,7 @@
 // added with 64-bit integer atomics (exact, order independent).  O(n^2)
 // comparisons, ALU bound.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "rwc_common.cuh"
@@ -49,6 +50,28 @@ __global__ void mre_final(int nb, int64_t n, const double *part, double *out) {
         __syncthreads();
     }
     if (threadIdx.x == 0) *out = sh[0] / (double)n;
+}
+
+// Predicted MRE (variance law of the visit counts): block partial sums of
+// sqrt(t (t - 1) / T) / (pi_u |H_u|) over u != v, t = sums_u / T.
+__global__ void pmre_partial(int64_t n, const double *d, double vol, int32_t v, const double *sums,
+                             double invT, const double *H, double *part) {
+    __shared__ double sh[MRE_THREADS];
+    double acc = 0.0;
+    for (int64_t u = blockIdx.x * (int64_t)MRE_THREADS + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * MRE_THREADS) {
+        if (u == v) continue;
+        const double t = sums[u] * invT;
+        const double se = sqrt(fmax(t * (t - 1.0), 0.0) * invT) / (d[u] / vol);
+        acc += se / fabs(H[u]);
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = MRE_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
 constexpr int KT_THREADS = 256;
@@ -163,5 +186,33 @@ extern "C" rwc_status rwc_kendall(int64_t n, const double *a, const double *b, i
         RWC_CUDA_TRY(cudaStreamSynchronize(stream));
         *host_tau = n >= 2 ? 2.0 * (double)s / ((double)n * (double)(n - 1)) : 0.0;
     }
+    return RWC_OK;
+}
+
+extern "C" rwc_status rwc_predict_mre(rwc_graph_t *G, const double *sums, int64_t num_trees,
+                                      const double *H, double target, double *host_mre,
+                                      int64_t *host_trees, rwc_stream_t stream_) {
+    using namespace rwc;
+    clear_error();
+    if (!G || !sums || !H || !host_mre || num_trees <= 0)
+        return set_error(RWC_ERR_INVALID, "rwc_predict_mre: graph, sums, H, host_mre and num_trees > 0 required");
+    const DevGraph &g = G->g;
+    const int64_t n = g.n;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const int nb = (int)std::min<int64_t>(MRE_BLOCKS, (n + MRE_THREADS - 1) / MRE_THREADS);
+    double *part = nullptr;
+    RWC_CUDA_TRY(cudaMallocAsync(&part, sizeof(double) * (nb + 1), stream));
+    count_launches(2);
+    pmre_partial<<<nb, MRE_THREADS, 0, stream>>>(n, g.d, g.vol, g.root, sums, 1.0 / (double)num_trees, H, part);
+    mre_final<<<1, MRE_THREADS, 0, stream>>>(nb, n, part, part + nb);
+    cudaError_t e = cudaGetLastError();
+    double m = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&m, part + nb, sizeof(double), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    cudaFreeAsync(part, stream);
+    RWC_CUDA_TRY(e);
+    *host_mre = std::sqrt(2.0 / M_PI) * m;
+    if (host_trees && target > 0.0)
+        *host_trees = (int64_t)std::ceil((double)num_trees * (*host_mre / target) * (*host_mre / target));
     return RWC_OK;
 }

@@ -87,3 +87,24 @@ def test_tree_count_sweep_small_config():
     for a, b in zip(mres, mres[1:]):
         assert 0.5 * 0.75 < b / a < 0.5 * 1.25, mres
     assert taus[0] < taus[1] < taus[2] < 1.0, taus
+
+
+@pytest.mark.parametrize("gname", ["ba", "weighted", "rmat12"])
+def test_predicted_mre_matches_oracle(gname):
+    """The stopping rule on the device against the oracle's formula on the
+    same sums and H (a sum in another order: 1e-12 relative); the trees for
+    a target follow from it."""
+    import synth
+    from oracle import apprwc
+    from oracle import wilson as ow
+    g = {"ba": lambda: synth.ba(2000, 3, seed=0),
+         "weighted": lambda: synth.rgg(600, 10.0, seed=2, sigma=0.5),
+         "rmat12": lambda: synth.rmat(12, 16, seed=3)}[gname]()
+    G = rwc.Graph.from_synth(g)
+    T = 300
+    sums, _, _, _ = G.sample(T, seed=1)
+    H = G.estimate(sums, T)
+    m, trees = rwc.rwc_predict_mre(G.handle, sums, T, H, target=0.01)
+    want = apprwc.predicted_mre(ow.wdeg(g), G.root, sums.cpu().numpy(), T, H.cpu().numpy())
+    assert m == pytest.approx(want, rel=1e-12, abs=0)
+    assert abs(trees - apprwc.trees_for(m, T, 0.01)) <= 1
