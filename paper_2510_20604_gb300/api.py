@@ -89,6 +89,27 @@ def fastwalk(graph: Graph, num_trees: int, seed: int = 1, tol: float = 1e-10, st
     return graph.estimate(sums, num_trees, tol=tol, stream=stream), st
 
 
+def fastwalk_to_target(graph: Graph, target_mre: float, first_trees: int = 256,
+                       max_trees: int = 1 << 22, seed: int = 1, tol: float = 1e-10, stream=None):
+    """FastWalk with the variance-law stopping rule: sample ``first_trees``,
+    estimate, and while the predicted MRE (rwc_predict_mre) exceeds the target
+    add the trees it says are missing (trees continue the same global ids, so
+    the result equals one run of the final count).  Returns (H, trees used,
+    predicted MRE)."""
+    if not target_mre > 0:
+        raise ValueError("target_mre must be positive")
+    T = max(1, int(first_trees))
+    sums, _, _, _ = graph.sample(T, seed=seed, stream=stream)
+    while True:
+        H = graph.estimate(sums, T, tol=tol, stream=stream)
+        mre, need = B.rwc_predict_mre(graph.handle, sums, T, H, target_mre, stream)
+        if mre <= target_mre or T >= max_trees:
+            return H, T, mre
+        extra = min(max(need, T + 1) - T, max_trees - T)
+        graph.sample(extra, seed=seed, tree0=T, sums=sums, stream=stream)
+        T += extra
+
+
 class Batch:
     def __init__(self, graphs):
         """graphs: sequence of objects with row_ptr, col, w (synth.Graph)."""

@@ -114,3 +114,20 @@ def test_estimate_rejects_bad_arguments():
         rwc.rwc_estimate(G.handle, s, 0, 1e-10, H)
     with pytest.raises(TypeError):
         rwc.rwc_estimate(G.handle, s.float(), 1, 1e-10, H)
+
+
+def test_fastwalk_to_target_stops_at_the_predicted_count():
+    """The stopping rule in the pipeline: starting from 200 trees on the
+    small configuration, trees are added until the predicted MRE is at most
+    1%; the result equals one run of the final tree count (the added trees
+    continue the global ids), and the measured MRE against the exact RWC is
+    near the target."""
+    g = synth.ba(2000, 3, seed=0)
+    G = rwc.Graph.from_synth(g)
+    H, T, mre = rwc.fastwalk_to_target(G, 0.01, first_trees=200, seed=1)
+    assert T > 200 and mre <= 0.01
+    H1, _ = rwc.fastwalk(G, T, seed=1)
+    assert torch.allclose(H, H1, rtol=1e-9, atol=0)
+    Hx = exact.rwc_pinv(g)
+    measured = float(np.mean(np.abs(H.cpu().numpy() - Hx) / Hx))
+    assert measured < 0.0125, measured
