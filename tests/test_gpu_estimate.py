@@ -28,9 +28,12 @@ def _hub_graph():
     return synth.from_edges(3000, np.array(a), np.array(b))
 
 
-@pytest.mark.parametrize("gname", ["ba", "weighted", "grid", "hub", "rmat13w"])
+@pytest.mark.parametrize("gname", ["ba", "weighted", "grid", "hub", "rmat13w", "multi", "multiw"])
 def test_pivot_column_and_recovery(gname):
-    g = {"ba": lambda: synth.ba(500, 3, seed=1),
+    from _graphs import multigraph
+    g = {"multi": lambda: multigraph(False),
+         "multiw": lambda: multigraph(True),
+         "ba": lambda: synth.ba(500, 3, seed=1),
          "weighted": lambda: synth.rgg(600, 10.0, seed=2, sigma=0.5),
          "grid": lambda: synth.grid2d(20, 23),
          "hub": _hub_graph,

@@ -9,6 +9,7 @@ import torch
 
 import paper_2510_20604_gb300 as rwc
 import synth
+from _graphs import multigraph
 from oracle import wilson as ow
 
 pytestmark = pytest.mark.gpu
@@ -165,3 +166,11 @@ def test_full_size_sampled_trees(which):
     assert np.array_equal(par.cpu().numpy(), ref["parents"])
     assert np.array_equal(vis.cpu().numpy(), ref["visits"])
     _check_tree(g, G.root, par[0].cpu().numpy())
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+@pytest.mark.parametrize("mode", ["shared", "global", "walker"])
+def test_parallel_arcs_bit_exact(mode, weighted):
+    g = multigraph(weighted)
+    assert (np.diff(g.col)[np.diff(g.src()) == 0] == 0).any()   # some parallel arcs
+    assert_exact(g, 29, MODES[mode])
