@@ -64,3 +64,19 @@ def test_autograd_function_backward():
     (H * c).sum().backward()
     ref = og.grad_closed(g.n, a, b, w, c.cpu().numpy())
     assert np.max(np.abs(wt.grad.cpu().numpy() - ref)) <= 1e-3 * np.abs(ref).max()
+
+
+def test_exact_gradient_on_parallel_arcs():
+    """A weighted graph with doubled and tripled edges: one gradient entry per
+    (a < b) arc, parallel copies equal, against the dense closed form."""
+    from _graphs import multigraph
+    g = multigraph(True)
+    G = rwc.Graph.from_synth(g)
+    c = synth.uniform_vector(g.n, 5)
+    ct = torch.tensor(c, dtype=torch.float64, device="cuda")
+    gg = G.grad(ct, k=0, tol=1e-10).double().cpu().numpy()
+    a, b, w = _edges(g)
+    ref = og.grad_closed(g.n, a, b, w, c)
+    assert np.max(np.abs(gg - ref)) <= 1e-3 * np.abs(ref).max()
+    same = (np.diff(a) == 0) & (np.diff(b) == 0)
+    assert same.any() and np.allclose(gg[1:][same], gg[:-1][same], rtol=1e-6, atol=0)
