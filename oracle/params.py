@@ -73,7 +73,8 @@ def spectral_radius_pv(g, v: int) -> float:
     d = degrees(g)
     W = np.zeros((n, n))
     src = g.src()
-    W[src, g.col] += (g.w.astype(np.float64) if g.w is not None else 1.0)
+    np.add.at(W, (src, g.col.astype(np.int64)),
+              g.w.astype(np.float64) if g.w is not None else 1.0)   # parallel arcs add up
     s = 1.0 / np.sqrt(d)
     M = s[:, None] * W * s[None, :]
     keep = np.arange(n) != v

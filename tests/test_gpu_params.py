@@ -23,6 +23,7 @@ GRAPHS = {
     "ba": lambda: synth.ba(500, 3, seed=1),
     "rmat12": lambda: synth.rmat(12, 8, seed=2),
     "weighted": lambda: synth.rgg(600, 10.0, seed=2, sigma=0.5),
+    "parallel_arcs": lambda: __import__("_graphs").multigraph(True),
 }
 
 

@@ -63,3 +63,21 @@ def test_formulas_hand_evaluated():
     p = op.auto_params(synth.complete(4), 0, 0.1)
     assert p["diameter"] == 1 and p["lambda"] == pytest.approx(2 / 3, abs=1e-13)
     assert p["trees"] == op.tree_count(0.1, 4, p["t"])
+
+
+def test_lambda_of_parallel_arcs_is_that_of_summed_weights():
+    """Parallel arcs act as one edge of summed weight: the multigraph's
+    spectral radius equals that of the simple graph with merged weights."""
+    from _graphs import multigraph
+    for weighted in (False, True):
+        g = multigraph(weighted)
+        a, b, w = g.undirected()
+        w = np.ones(len(a)) if w is None else w.astype(np.float64)
+        key = a * g.n + b
+        uk, inv = np.unique(key, return_inverse=True)
+        ws = np.zeros(len(uk))
+        np.add.at(ws, inv, w)
+        simple = synth.from_edges(g.n, uk // g.n, uk % g.n, ws.astype(np.float32))
+        lam_m = op.spectral_radius_pv(g, 0)
+        lam_s = op.spectral_radius_pv(simple, 0)
+        assert lam_m == pytest.approx(lam_s, rel=1e-6)
