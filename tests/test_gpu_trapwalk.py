@@ -15,9 +15,11 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("gname,flags", [("ba", 0), ("weighted", 0), ("grid", 0),
-                                         ("weighted", rwc.GRAPH_INT64_OFFSETS)])
+                                         ("weighted", rwc.GRAPH_INT64_OFFSETS), ("parallel_arcs", 0)])
 def test_trap_walk_counts_bit_exact(gname, flags):
-    g = {"ba": lambda: synth.ba(400, 3, seed=2),
+    from _graphs import multigraph
+    g = {"parallel_arcs": lambda: multigraph(True),
+         "ba": lambda: synth.ba(400, 3, seed=2),
          "weighted": lambda: synth.rgg(300, 9.0, seed=3, sigma=0.8),
          "grid": lambda: synth.grid2d(13, 17)}[gname]()
     G = rwc.Graph.from_synth(g, flags=flags)
