@@ -33,6 +33,11 @@
  *    -1 at the in-tree endpoint); the 1/l scaling is applied once by the
  *    caller (Section 5, the estimator t~_u = sum_i t~_ui / l).
  *
+ *  - trap_walks: the straightforward estimator Section 5 starts from (walks
+ *    from every u stopped at the pivot, counting their visits to u), with
+ *    Philox counter (step, u, walk, 0xFFFFFFFE) and the RandomNeighbor rule
+ *    of succ().
+ *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared -pthread (see build.py).
  */
 #include <stdint.h>
