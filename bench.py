@@ -176,15 +176,16 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_baseline(workload, budget_s=20.0):
-    """Oracle sequential Wilson on the host cores, bounded sample per graph.
-    Returns (trees/s for the workload's tree mix, details)."""
+def cpu_baseline(workload, budget_s=20.0, graphs=None):
+    """Oracle sequential Wilson on the host cores, bounded sample per graph
+    (graphs: key -> graph already built, else made here).  Returns (trees/s
+    for the workload's tree mix, details)."""
     from oracle import wilson as ow
     cores = ow.cores()
     per_tree = {}
     detail = []
     for key, T in WORKLOADS[workload]:
-        g = make_graph(key)
+        g = graphs[key] if graphs else make_graph(key)
         s = ow.Sampler(g, seed=1)
         done, t_used, draws = 0, 0.0, 0
         tree0 = 1_000_000
@@ -202,16 +203,41 @@ def cpu_baseline(workload, budget_s=20.0):
     return total_T / est, cores, "; ".join(detail) + " (all cores, one tree per thread; scaled to the full tree counts)"
 
 
+def cpu_single_thread(workload, budget_s=5.0, graphs=None):
+    """The oracle on one host thread (the paper's setting), one tree at a
+    time, bounded sample per graph (graphs as in cpu_baseline).  Returns
+    (trees/s for the workload's tree mix, details)."""
+    from oracle import wilson as ow
+    per_tree = {}
+    detail = []
+    for key, T in WORKLOADS[workload]:
+        g = graphs[key] if graphs else make_graph(key)
+        s = ow.Sampler(g, seed=1)
+        done, t_used, draws = 0, 0.0, 0
+        while t_used < budget_s / len(WORKLOADS[workload]) and done < T:
+            t0 = time.perf_counter()
+            out = s.sample(2_000_000 + done, 1, nthreads=1)
+            t_used += time.perf_counter() - t0
+            done += 1
+            draws += out["draws"]
+        per_tree[key] = t_used / done
+        detail.append(f"{key}: {done} trees ({draws} draws) in {t_used:.2f} s")
+    total_T = sum(T for _, T in WORKLOADS[workload])
+    est = sum(per_tree[key] * T for key, T in WORKLOADS[workload])
+    return total_T / est, "; ".join(detail) + " (one thread; scaled to the full tree counts)"
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
     vals = []
     samples = []
     cores = 1
+    built = {key: make_graph(key) for key, _ in WORKLOADS[args.workload]}
     for _ in range(args.warmup):
-        cpu_baseline(args.workload, budget_s=2.0)
+        cpu_baseline(args.workload, budget_s=2.0, graphs=built)
     for _ in range(args.steps):
-        v, cores, samp = cpu_baseline(args.workload, budget_s=args.ref_budget)
+        v, cores, samp = cpu_baseline(args.workload, budget_s=args.ref_budget, graphs=built)
         vals.append(v)
         samples.append(samp)
     total_T = sum(T for _, T in WORKLOADS[args.workload])
@@ -473,8 +499,14 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, samp = cpu_baseline(args.workload)
+        built = {key: g for key, T, g, G, sums in graphs}
+        v, cores, samp = cpu_baseline(args.workload, graphs=built)
         cpu = {"value": v, "unit": "trees/s", "cores": cores, "kind": "oracle", "sample": samp}
+        try:   # the paper's setting, reported beside the all-core baseline
+            v1, samp1 = cpu_single_thread(args.workload, graphs=built)
+            cpu["single_thread"] = {"value": v1, "unit": "trees/s", "cores": 1, "sample": samp1}
+        except Exception as exc:  # a failed extra measurement must not cost the line
+            cpu["single_thread"] = {"error": str(exc)[:200]}
 
     if rank == 0:
         line = {
