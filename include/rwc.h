@@ -203,10 +203,11 @@ rwc_status rwc_sample_trees(rwc_graph_t *g, uint64_t seed, int64_t tree0,
 /*
  * rwc_sample_trees without any allocation (the paper has no counterpart).
  *
- * For callers that cannot allocate device memory while they sample: code
- * running while a stream is being captured into a CUDA graph, real-time or
- * embedded hosts that allow no allocation after start-up, and processes whose
- * memory pool is exhausted or owned by another allocator.  It samples the
+ * For callers that cannot allocate device memory while they sample:
+ * real-time or embedded hosts that allow no allocation after start-up (an
+ * allocation can block or fail at an unpredictable moment), and processes
+ * whose device memory pool is exhausted or owned by another allocator that
+ * the library cannot draw from.  It samples the
  * same trees as rwc_sample_trees (identical sums, parents and visits; the
  * concurrent-walker sampler) but keeps all of its scratch in one static
  * device array of RWC_NOALLOC_SCRATCH_BYTES inside this library, which every
@@ -219,7 +220,7 @@ rwc_status rwc_sample_trees(rwc_graph_t *g, uint64_t seed, int64_t tree0,
  *    does not fit (n above roughly 2 million) gets RWC_ERR_INVALID.  Trees
  *    are processed in as many chunks as the array requires.
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    (cudaGetSymbolAddress) once, with that device current.
  *  - Every call on a device shares the one array, which keeps the last call's
  *    contents (the call clears what must start at zero); calls that overlap
  *    on the GPU (other streams, other host threads) race and corrupt each

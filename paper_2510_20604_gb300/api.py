@@ -167,18 +167,31 @@ class Batch:
 
 
 def _edge_index(row_ptr, col):
-    """For every arc, the index of its undirected edge in (a < b) CSR order."""
+    """For every arc, the index of its undirected edge in (a < b) CSR order.
+    Parallel arcs are paired in order: the k-th arc b -> a of a key {a, b}
+    gets the edge of the k-th arc a -> b."""
     n = len(row_ptr) - 1
     src = np.repeat(np.arange(n, dtype=np.int64), np.diff(row_ptr))
     dst = col.astype(np.int64)
     up = src < dst
     eid = np.full(len(col), -1, np.int64)
-    eid[up] = np.arange(int(up.sum()))
-    keys_up = src[up] * n + dst[up]
-    order = np.argsort(keys_up, kind="stable")
-    lo_keys = dst[~up] * n + src[~up]
-    pos = np.searchsorted(keys_up[order], lo_keys, side="left")
-    eid[~up] = np.arange(int(up.sum()))[order][pos]
+    n_up = int(up.sum())
+    eid[up] = np.arange(n_up)
+
+    def keyed(key):
+        # arcs sorted by (key, position), and each arc's rank among equal keys
+        order = np.argsort(key, kind="stable")
+        k = key[order]
+        first = np.r_[True, k[1:] != k[:-1]]
+        start = np.maximum.accumulate(np.where(first, np.arange(len(k)), 0))
+        return order, k, np.arange(len(k)) - start
+
+    o_up, k_up, r_up = keyed(src[up] * n + dst[up])
+    o_dn, k_dn, r_dn = keyed(dst[~up] * n + src[~up])
+    if not (np.array_equal(k_up, k_dn) and np.array_equal(r_up, r_dn)):
+        raise ValueError("arcs are not paired with their reverses")
+    dn_idx = np.nonzero(~up)[0]
+    eid[dn_idx[o_dn]] = np.arange(n_up)[o_up]
     return eid
 
 

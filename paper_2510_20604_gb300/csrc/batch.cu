@@ -397,8 +397,9 @@ extern "C" rwc_status rwc_autotune(rwc_batch_t *b, const char *cache_path, rwc_s
             fclose(f);
             buf[len] = 0;
             const char *p = strstr(buf, sig);
+            const char *colon = p ? strchr(p, ':') : nullptr;
             int t0, t1, tl, cs;
-            if (p && sscanf(strchr(p, ':') + 1, " [%d, %d, %d, %d]", &t0, &t1, &tl, &cs) == 4) {
+            if (colon && sscanf(colon + 1, " [%d, %d, %d, %d]", &t0, &t1, &tl, &cs) == 4) {
                 b->threads[0] = t0; b->threads[1] = t1; b->tile = tl; b->class_split = cs;
                 b->items_T = -1;
                 return RWC_OK;

@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <atomic>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
@@ -161,13 +162,16 @@ __device__ __forceinline__ int32_t succ(const DevGraph &g, int32_t u, uint32_t c
 // Library-wide kernel launch counter (graph.cu).
 void count_launches(int64_t k);
 
+// SM count of the current device, cached per device index.
 inline int num_sms() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+    int sms = dev < 64 ? cache[dev].load(std::memory_order_relaxed) : 0;
+    if (sms <= 0) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 1;
+        if (dev < 64) cache[dev].store(sms, std::memory_order_relaxed);
     }
     return sms;
 }

@@ -659,9 +659,9 @@ rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, 
 
 // ---------------------------------------------------------------------------
 // Allocation-free sampling.  Some callers cannot allocate device memory while
-// they sample: code that runs while a CUDA stream is being captured into a
-// graph, real-time or embedded hosts that forbid allocation after start-up,
-// and processes whose memory pool is exhausted or owned by another allocator.
+// they sample: real-time or embedded hosts that forbid allocation after
+// start-up, and processes whose memory pool is exhausted or owned by another
+// allocator.
 // rwc_sample_trees_noalloc samples with the walker kernels above, keeping all
 // of its scratch (start order, per-tree vertex words, requeue buffers and
 // counters) in one fixed array of this file; the caller still passes the

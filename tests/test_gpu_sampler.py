@@ -153,19 +153,82 @@ def _check_tree(g, root, par):
     assert (p == root).all()
 
 
+def _check_trees_on_device(g, root, par, vis, draws):
+    """Properties every sampled tree must have, checked for all trees on the
+    device: the root has parent -1 and 0 visits, every other vertex has at
+    least one visit and a parent among its neighbours, the visits add up to
+    the draws, and following parents from any vertex reaches the root
+    (pointer doubling)."""
+    dev = par.device
+    n = g.n
+    # arcs as sorted keys u * n + w (rows ascending, each row sorted)
+    keys = torch.as_tensor(g.src().astype(np.int64) * n + g.col.astype(np.int64), device=dev)
+    assert bool((keys[1:] >= keys[:-1]).all())
+    assert bool((par[:, root] == -1).all()) and bool((vis[:, root] == 0).all())
+    nonroot = torch.ones(n, dtype=torch.bool, device=dev)
+    nonroot[root] = False
+    u = torch.arange(n, device=dev)[nonroot]
+    assert int(vis.sum(dtype=torch.int64)) == draws
+    for t in range(par.shape[0]):
+        assert bool((vis[t, nonroot] >= 1).all()), t
+        p = par[t].long()
+        want = u * n + p[nonroot]
+        pos = torch.clamp(torch.searchsorted(keys, want), max=keys.numel() - 1)
+        assert bool((keys[pos] == want).all()), t
+        q = p.clone()
+        q[root] = root
+        for _ in range(24):          # reaches 2^24 > n ancestors
+            q = q[q]
+        assert bool((q == root).all()), t
+
+
 @pytest.mark.parametrize("which", ["grid1024", "rmat20"])
-def test_full_size_sampled_trees(which):
-    """Benchmark graphs at full size, in the benchmark's launch configuration
-    (GLOBAL mode, auto chunk): a few trees, each compared with the oracle."""
+def test_full_size_bench_launch_config(which):
+    """The benchmark's own launch at full size: 2000 trees resident at once,
+    default options (automatic walkers per tree and conflict policy, which
+    give 64 walkers and the fresh-start policy for this many trees).  Every
+    tree is checked on the device for the spanning-tree properties, four
+    chosen trees bit for bit against the oracle's sequential Wilson, and on
+    R-MAT 20 the sums of all 2000 trees against the oracle's."""
     g = synth.grid2d(1024, 1024) if which == "grid1024" else synth.rmat(20, 16, seed=0)
     G = rwc.Graph.from_synth(g)
-    T = 2 if which == "grid1024" else 4
-    tree0 = 1000
-    sums, st, par, vis = G.sample(T, seed=1, tree0=tree0, want_trees=True)
-    ref = ow.Sampler(g, root=G.root, seed=1).sample(tree0, T, want_trees=True, nthreads=T)
-    assert np.array_equal(par.cpu().numpy(), ref["parents"])
-    assert np.array_equal(vis.cpu().numpy(), ref["visits"])
-    _check_tree(g, G.root, par[0].cpu().numpy())
+    T = 2000
+    sums, st, par, vis = G.sample(T, seed=1, tree0=0, want_trees=True, opt=rwc.Options(profile=1))
+    assert st.mode == rwc.MODE_WALKER and st.block_threads == 64 and st.chunks == 1
+    s = ow.Sampler(g, root=G.root, seed=1)
+    for t in (0, 1, 997, 1999):
+        ref = s.sample(t, 1, want_trees=True)
+        assert np.array_equal(par[t].cpu().numpy(), ref["parents"][0]), t
+        assert np.array_equal(vis[t].cpu().numpy(), ref["visits"][0]), t
+    _check_trees_on_device(g, G.root, par, vis, int(st.draws))
+    if which == "rmat20":
+        ref = s.sample(0, T, nthreads=ow.cores())
+        assert np.array_equal(sums.cpu().numpy(), ref["sums"])
+    else:
+        assert float(sums.sum().item()) == float(st.draws)
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_graph_create_pivot_is_oracle_max_degree_root(weighted):
+    """rwc_graph_create's pivot (root = -1): the largest weighted degree, ties
+    to the smallest id, as the oracle computes it; on graphs built with tied
+    maximum degrees (grids: four-way ties; weighted: equal weight sums at
+    several vertices)."""
+    cases = [synth.grid2d(7, 9), synth.grid2d(40, 40), synth.ba(500, 3, seed=5)]
+    if weighted:
+        g0 = synth.grid2d(12, 12)
+        # weights from a symmetric function of the endpoints that makes
+        # several vertices share the largest weighted degree
+        src = g0.src()
+        w = (1.0 + ((src % 3) == 0) + ((g0.col % 3) == 0)).astype(np.float32)
+        cases = [synth.Graph(g0.n, g0.row_ptr, g0.col, w), synth.rgg(400, 8.0, seed=2, sigma=1.0)]
+    for g in cases:
+        G = rwc.Graph.from_synth(g)
+        d = ow.wdeg(g)
+        top = np.nonzero(d == d.max())[0]
+        assert G.root == ow.max_degree_root(g) == int(top[0])
+        if not weighted:
+            assert len(top) > 1 or g.n == 500
 
 
 @pytest.mark.parametrize("weighted", [False, True])

@@ -1,9 +1,9 @@
 """The allocation-free sampling entry point (rwc_sample_trees_noalloc).
 
-Callers that cannot allocate device memory while sampling (stream capture in
-progress, hosts that forbid allocation after start-up, exhausted or foreign
-memory pools) use this entry point; it keeps its scratch in a static device
-array of the library.  These tests call it through the C ABI twice in a row
+Callers that cannot allocate device memory while sampling (hosts that forbid
+allocation after start-up, exhausted device memory pools, or pools owned by an
+allocator the library cannot draw from) use this entry point; it keeps its
+scratch in a static device array of the library.  These tests call it through the C ABI twice in a row
 and compare with rwc_sample_trees.  The file is named so that pytest collects
 it last; it also passes when run alone in a fresh process.
 """
