@@ -98,6 +98,11 @@ typedef struct {
                                  changes owner), 3 = yield and take a fresh start
                                  at once while fresh starts remain (the wait of 1
                                  once only requeued starts are left) */
+    int64_t max_wait_ns;      /* WALKER mode: a wait inside the sampler fails with
+                                 RWC_ERR_NOT_CONVERGED once its thread block (one
+                                 tree) has stored no vertex word for this many
+                                 nanoseconds (0 = 30 s); the bound is on a lack of
+                                 progress, not on the length of any one wait */
 } rwc_options_t;
 
 /* Sampler phases reported in rwc_stats_t.  GLOBAL mode: INIT, WALK, POP

@@ -34,12 +34,13 @@ class Options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
                 ("trees_per_chunk", ctypes.c_int64), ("use_jumps", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("memory_budget", ctypes.c_int64),
-                ("profile", ctypes.c_int32), ("walker_policy", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("walker_policy", ctypes.c_int32),
+                ("max_wait_ns", ctypes.c_int64)]
 
     def __init__(self, mode=0, max_rounds=0, trees_per_chunk=0, use_jumps=-1, block_threads=0,
-                 memory_budget=0, profile=0, walker_policy=0):
+                 memory_budget=0, profile=0, walker_policy=0, max_wait_ns=0):
         super().__init__(mode, max_rounds, trees_per_chunk, use_jumps, block_threads,
-                         memory_budget, profile, walker_policy)
+                         memory_budget, profile, walker_policy, max_wait_ns)
 
 
 class Params(ctypes.Structure):

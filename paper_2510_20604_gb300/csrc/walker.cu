@@ -141,19 +141,23 @@ __global__ void __maxnreg__(RWC_WALKER_MAXNREG) w_trees(DevGraph g, WState s, in
     __shared__ int sh_rhead, sh_rtail;  // retry queue
     __shared__ int sh_active;           // walkers holding a start
     __shared__ int sh_err;
-    extern __shared__ int sh[];         // prio[W], kill[W], killer[W], ver[W], killv[W]
+    __shared__ unsigned sh_prog;        // rewritten by every walker that stores a vertex word
+    // prio[W], kill[W], killer[W], ver[W], killv[W], wprog[W] (24 W bytes), then wt0[W]
+    extern __shared__ __align__(8) int sh[];
     int *prio = sh;
     int *kill = sh + blockDim.x;
     int *killer = sh + 2 * blockDim.x;
     int *ver = sh + 3 * blockDim.x;
     int *killv = sh + 4 * blockDim.x;   // the contested vertex of a yield request
+    unsigned *wprog = (unsigned *)(sh + 5 * blockDim.x);   // block progress seen when a wait began
+    uint64_t *wt0 = (uint64_t *)(sh + 6 * blockDim.x);   // time of that sighting
     unsigned long long steps = 0, yields = 0, pops = 0;
     unsigned long long it_state[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 
     for (;;) {
         if (threadIdx.x == 0) {
             sh_tree = (int)atomicAdd(&s.ctr[3], 1ull);
-            sh_next = 0; sh_rhead = 0; sh_rtail = 0; sh_active = 0; sh_err = 0;
+            sh_next = 0; sh_rhead = 0; sh_rtail = 0; sh_active = 0; sh_err = 0; sh_prog = 0;
         }
         prio[threadIdx.x] = INF;
         kill[threadIdx.x] = -1;
@@ -176,15 +180,26 @@ __global__ void __maxnreg__(RWC_WALKER_MAXNREG) w_trees(DevGraph g, WState s, in
         int32_t pend_start = -1;
         int walked = 0;          // vertices visited in the current POP/REL/SET pass
         uint32_t polls = 0;
-        uint64_t wait_t0 = 0;
         auto vread = [](const int *a) { return *(const volatile int *)a; };
         auto bump = [&]() { *(volatile int *)&ver[me] = ver[me] + 1; };
-        // returns true when the current wait has exceeded its time bound
+        // true when the block has made no progress (no vertex word stored by
+        // any of its walkers) for max_wait_ns while this walker waited: waits
+        // are bounded by a lack of progress, not by their own length
         auto waited_out = [&]() {
-            if (polls++ == 0) wait_t0 = gtimer();
-            if ((polls & 1023) == 0 && gtimer() - wait_t0 > (uint64_t)max_wait_ns) {
-                atomicOr(&sh_err, WERR_WAIT);
-                return true;
+            if (polls++ == 0) {
+                wprog[me] = *(volatile unsigned *)&sh_prog;
+                wt0[me] = gtimer();
+                return false;
+            }
+            if ((polls & 255) == 0) {
+                const unsigned pr = *(volatile unsigned *)&sh_prog;
+                if (pr != wprog[me]) {
+                    wprog[me] = pr;
+                    wt0[me] = gtimer();
+                } else if (gtimer() - wt0[me] > (uint64_t)max_wait_ns) {
+                    atomicOr(&sh_err, WERR_WAIT);
+                    return true;
+                }
             }
             return false;
         };
@@ -219,6 +234,7 @@ __global__ void __maxnreg__(RWC_WALKER_MAXNREG) w_trees(DevGraph g, WState s, in
         for (;;) {
             const bool err = vread(&sh_err) != 0;
             if (__any_sync(0xffffffffu, err)) break;
+
             if (__all_sync(0xffffffffu, state == S_DONE)) break;
             // a warp whose walkers all wait gives its issue slots to the others
             if (__all_sync(0xffffffffu, state == S_DONE || state == S_WAITV || state == S_WAITK ||
@@ -420,6 +436,9 @@ __global__ void __maxnreg__(RWC_WALKER_MAXNREG) w_trees(DevGraph g, WState s, in
             }
 
             // ---- memory: store, claim (in flight during the draw), draw
+            // a stored word marks the block as progressing: any new value of
+            // sh_prog restarts the waits' clocks (the SM clock keeps it changing)
+            if (s_v >= 0 || c_v >= 0) *(volatile unsigned *)&sh_prog = (unsigned)clock();
             if (s_v >= 0) stv(st + s_v, s_val);
             uint64_t old = 0;
             if (c_v >= 0) old = cas_cta(st + c_v, c_cmp, c_val);
@@ -492,6 +511,10 @@ __global__ void w_accum(int64_t n, int32_t root, const uint64_t *word, int64_t B
     for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(draws, local);
 }
+
+// Dynamic shared memory of a walker block of W threads: six int arrays and
+// one uint64 array (24 W bytes keep it 8-byte aligned).
+inline size_t walker_smem(int W) { return (size_t)W * (6 * sizeof(int) + 8); }
 
 template <class F>
 void dispatch(const DevGraph &g, F f) {
@@ -573,7 +596,8 @@ rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, 
         cudaEvent_t *e; bool on;
         ~EvFree() { if (on) for (int i = 0; i < 6; ++i) cudaEventDestroy(e[i]); }
     } evf{ev, prof};
-    const int64_t max_wait = (int64_t)30 * 1000000000;   // 30 s per wait (ns)
+    // a wait fails when its block made no progress for this long (ns)
+    const int64_t max_wait = o.max_wait_ns > 0 ? o.max_wait_ns : (int64_t)30 * 1000000000;
     const int sms = num_sms();
     int64_t *h = G->host_scalars;
     for (int64_t c0 = 0; c0 < T; c0 += B) {
@@ -595,11 +619,11 @@ rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, 
                 Wc = 64;
                 for (int cand = 512; cand >= 64; cand -= 32) {
                     int ps = 0;
-                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, kern, cand, 5 * (size_t)cand * sizeof(int));
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, kern, cand, walker_smem(cand));
                     if ((int64_t)sms * ps >= Bc) { Wc = cand; break; }
                 }
             }
-            const size_t smem = 5 * (size_t)Wc * sizeof(int);
+            const size_t smem = walker_smem(Wc);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Wc, smem);
             if (per_sm < 1) { status = set_error(RWC_ERR_UNSUPPORTED, "walker block does not fit"); return; }
             const int64_t blocks = std::min<int64_t>(Bc, (int64_t)sms * per_sm);
@@ -773,7 +797,7 @@ extern "C" rwc_status rwc_sample_trees_noalloc(rwc_graph_t *G, uint64_t seed, in
         rwc_status status = RWC_OK;
         dispatch(g, [&](auto off64, auto wt) {
             auto kern = w_trees<decltype(off64)::value, decltype(wt)::value, false>;
-            const size_t smem = 5 * (size_t)W * sizeof(int);
+            const size_t smem = walker_smem(W);
             int per_sm = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W, smem);
             if (per_sm < 1) { status = set_error(RWC_ERR_UNSUPPORTED, "walker block does not fit"); return; }

@@ -237,3 +237,19 @@ def test_parallel_arcs_bit_exact(mode, weighted):
     g = multigraph(weighted)
     assert (np.diff(g.col)[np.diff(g.src()) == 0] == 0).any()   # some parallel arcs
     assert_exact(g, 29, MODES[mode])
+
+
+def test_walker_wait_bound_is_on_progress_not_elapsed_time():
+    """The walker's waits fail only after the tree's block stops storing
+    vertex words for max_wait_ns.  A 1 ms bound on a long-tailed tree (512 x
+    512 grid, 32 walkers, each tree running for far longer than 1 ms, with
+    walkers idling at the end while the last walks settle) must still finish,
+    and bit-exactly."""
+    g = synth.grid2d(512, 512)
+    opt = rwc.Options(mode=rwc.MODE_WALKER, block_threads=32, max_wait_ns=1_000_000, profile=1)
+    G = rwc.Graph.from_synth(g)
+    sums, st, par, vis = G.sample(4, seed=1, tree0=5, want_trees=True, opt=opt)
+    assert st.phase_ms[1] > 20.0     # the walker kernel ran far longer than 1 ms
+    ref = ow.Sampler(g, root=G.root, seed=1).sample(5, 4, want_trees=True, nthreads=4)
+    assert np.array_equal(par.cpu().numpy(), ref["parents"])
+    assert np.array_equal(vis.cpu().numpy(), ref["visits"])
