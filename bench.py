@@ -10,12 +10,20 @@ value    = trees per second over the timed steps (all ranks).
 e2e      = the same metric through the public API from host buffers: graph
            upload from pinned host memory (rwc_graph_create), sampling,
            estimate, and the read-back of H, every step.
-roofline = the dominant sampler kernel's algorithmic bytes per launch over
-           its CUDA-event duration, against the measured HBM copy bandwidth.
+roofline = the sampler's algorithmic bytes (per successor draw: row bounds,
+           arc head and, for weighted rows, the alias entry; per tree and
+           vertex: parent and visit count) over the device time of its
+           kernels, against the measured HBM copy bandwidth; the walker's own
+           state-word traffic and the ncu-measured DRAM traffic are reported
+           beside it.
+extras   = the paper-size R-MAT 24 (500 trees), the 4096-graph batch
+           (persistent launch against one launch per graph) and the gradient
+           on the 1e5-vertex geometric graph, measured in the same run.
 
-Under torchrun each rank samples its own tree range (weak scaling; no data
-collective).  `--impl reference` times the CPU oracle (sequential Wilson) on
-a bounded sample of the same workload.
+Under torchrun each rank samples its own tree range (weak scaling) and the
+ranks add their visit sums before the estimate.  `--impl reference` times
+the CPU oracle (sequential Wilson) on a bounded sample of the same workload
+per step.
 """
 from __future__ import annotations
 
@@ -29,6 +37,7 @@ import time
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+T_START = time.perf_counter()
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
@@ -49,31 +58,32 @@ KERNEL_NAMES = {1: {"init": "g_init", "walk": "g_walk", "pop": "g_pop", "accum":
                 3: {"init": "w_init", "walk": "w_trees", "accum": "w_accum"}}
 
 
-def bytes_per_unit(phase, mode, weighted, off64):
-    """Algorithmic bytes per work unit of each sampler phase.
-    mode: 1 round-based (GLOBAL), 2 shared memory, 3 concurrent walkers."""
-    row = 16 if off64 else 8
-    arc = 16 if weighted else 4
-    if mode == 3:   # walker kernel: per draw, row bounds + arc + state word read/write
-        return {"init": 8, "walk": row + arc + 16, "classify": 0, "pop": 0, "finish": 0,
-                "accum": 8}[phase]
-    if mode == 2:   # shared memory: per draw, the graph reads only
-        return {"init": 0, "walk": row + arc, "classify": 0, "pop": 0, "finish": 0, "accum": 0}[phase]
-    return {"init": row + arc + 12, "walk": 8, "classify": 5, "pop": row + arc + 12,
-            "finish": 9, "accum": 12}[phase]
+def bytes_per_draw(weighted, off64):
+    """Algorithmic bytes of one successor draw (the method's own traffic): the
+    row bounds of the vertex (2 x int32, or 2 x int64 offsets), the chosen
+    arc's head (int32) and, for weighted rows, its alias threshold and alias
+    (uint32 + int32)."""
+    return (16 if off64 else 8) + 4 + (8 if weighted else 0)
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# dominant kernel, from one ncu capture per workload; valid only for the kernel
-# source it was measured on (code_hash of the .cu file), else reported as null.
-TRAFFIC = {
-    # (workload, kernel): (bytes per launch, source file, sha256 of the source);
-    # captured with --metrics dram__bytes_read.sum,dram__bytes_write.sum (one
-    # pass, the full-size launches of the benchmark's own command)
-    ("grid1024+rmat20", "w_trees"): (6549618983296, "walker.cu",  # mean of the two launches
-                                     "f49c11e1e8726513496a7564ee7f4d0c5e37783339f7197f1f8cb05e520cebd1"),
-    ("grid1024", "w_trees"): (12348197538560, "walker.cu", "f49c11e1e8726513496a7564ee7f4d0c5e37783339f7197f1f8cb05e520cebd1"),
-    ("rmat20", "w_trees"): (751040428032, "walker.cu", "f49c11e1e8726513496a7564ee7f4d0c5e37783339f7197f1f8cb05e520cebd1"),
+# Per (tree, vertex): the tree's parent (int32) and visit count (int32).
+BYTES_PER_TREE_VERTEX = 8
+# Implementation traffic of the concurrent-walker sampler, not counted above:
+# each draw reads and writes back the vertex's 8-byte state word.
+IMPL_BYTES_PER_DRAW = 16
+
+
+def algorithmic_bytes(draws, trees, n, weighted, off64):
+    return draws * bytes_per_draw(weighted, off64) + trees * n * BYTES_PER_TREE_VERTEX
+
+
+# DRAM traffic of the walker kernel per successor draw, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch divided by its
+# draws) on a small case of each graph family; the benchmark scales it by the
+# draws of its own launches.  Valid only for the kernel source it was measured
+# on (code_hash of the .cu file), else reported as null.
+TRAFFIC_PER_DRAW = {
+    # family: (bytes per draw, case captured, source file, code hash)
 }
 
 
@@ -87,11 +97,17 @@ def code_hash(path):
     return hashlib.sha256("\n".join(code).encode()).hexdigest()
 
 
-def traffic_for(workload, kernel):
-    ent = TRAFFIC.get((workload, kernel))
+def family(key):
+    return "grid" if key.startswith("grid") else "rmat" if key.startswith("rmat") else key
+
+
+def traffic_per_draw(key):
+    """Measured DRAM bytes per draw of the walker kernel for this graph's
+    family, or None (no capture, or the kernel changed since)."""
+    ent = TRAFFIC_PER_DRAW.get(family(key))
     if not ent:
         return None
-    nbytes, src, sha = ent
+    nbytes, _case, src, sha = ent
     path = os.path.join(ROOT, "paper_2510_20604_gb300", "csrc", src)
     try:
         cur = code_hash(path)
@@ -228,29 +244,50 @@ def cpu_single_thread(workload, budget_s=5.0, graphs=None):
 
 
 def run_reference(args, rank):
+    """The oracle (sequential Wilson, C, one tree per host thread) on a
+    bounded sample of the workload per step: two trees per host core of every
+    graph, so a step keeps the workload's mix of graphs.  value = trees of the
+    step over its wall time, averaged over the timed steps."""
     if rank != 0:
         return
-    vals = []
-    samples = []
-    cores = 1
+    from oracle import wilson as ow
+    cores = ow.cores()
     built = {key: make_graph(key) for key, _ in WORKLOADS[args.workload]}
+    samplers = {key: ow.Sampler(g, seed=1) for key, g in built.items()}
+    per_graph = max(1, min(2 * cores, args.ref_trees)) if args.ref_trees else 2 * cores
+    next_tree = {key: 1_000_000 for key in built}
+
+    def ref_step():
+        t0 = time.perf_counter()
+        trees = 0
+        for key, T in WORKLOADS[args.workload]:
+            k = min(per_graph, T)
+            samplers[key].sample(next_tree[key], k, nthreads=cores)
+            next_tree[key] += k
+            trees += k
+        return trees, time.perf_counter() - t0
+
     for _ in range(args.warmup):
-        cpu_baseline(args.workload, budget_s=2.0, graphs=built)
+        ref_step()
+    vals, secs = [], []
+    trees = 0
     for _ in range(args.steps):
-        v, cores, samp = cpu_baseline(args.workload, budget_s=args.ref_budget, graphs=built)
-        vals.append(v)
-        samples.append(samp)
-    total_T = sum(T for _, T in WORKLOADS[args.workload])
+        trees, dt = ref_step()
+        vals.append(trees / dt)
+        secs.append(dt)
     value = float(np.mean(vals))
+    sample = (f"{trees} trees per step ({', '.join(f'{min(per_graph, T)} of {key}' for key, T in WORKLOADS[args.workload])}), "
+              f"{cores} threads, one tree per thread; {args.steps} steps")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "trees/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 * total_T / value, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1000.0 * float(np.mean(secs)), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
         "config": {"workload": args.workload, "trees": dict(WORKLOADS[args.workload]),
-                   "implementation": "oracle sequential Wilson (CPU), sampler only"},
+                   "implementation": "oracle sequential Wilson (CPU), sampling only; each step a bounded "
+                                     "sample with the workload's mix of graphs"},
         "cpu_baseline": {"value": value, "unit": "trees/s", "cores": cores, "kind": "oracle",
-                         "sample": samples[-1]},
+                         "sample": sample},
         "e2e": {"value": value, "unit": "trees/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -259,26 +296,31 @@ def run_reference(args, rank):
 METRIC = "spanning trees/s and RWC nodes/s at <=1% mean rel err; % of HBM roofline"
 
 
-def run_batch(args, rwc, torch, dev, world, rank):
+def batch_measure(rwc, torch, dev, steps, warmup, world=1):
     """4096 small graphs (sizes log-uniform in [50, 20000], ER / BA / RGG),
-    256 trees each: one persistent launch per size class, replayed from a CUDA
-    graph, against one launch per graph."""
+    256 trees each, autotuned schedule: one persistent launch (replayed from
+    a CUDA graph) against one launch per graph, same trees, same sums."""
     import synth
     T = WORKLOADS["batch4096"][0][1]
+    t0 = time.perf_counter()
     specs = synth.batch_specs(4096, seed=0)
     gs = [synth.batch_graph(i, n, kind, seed=0) for i, (n, kind) in enumerate(specs)]
     B = rwc.Batch(gs)
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
     B.autotune(None)
+    tune_s = time.perf_counter() - t0
     sums = torch.zeros(B.N, dtype=torch.float64, device=dev)
     res = {}
+    ref = None
     for name, kw in (("persistent_graph", dict(use_graph=1)), ("per_graph_launch", dict(per_graph_launch=1))):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             sums.zero_()
             B.sample(T, seed=1, sums=sums, **kw)
         torch.cuda.synchronize()
         t = []
         draws = 0
-        for _ in range(args.steps):
+        for _ in range(steps):
             sums.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -287,19 +329,113 @@ def run_batch(args, rwc, torch, dev, world, rank):
             torch.cuda.synchronize()
             t.append(e0.elapsed_time(e1))
             draws = st.draws
+        if ref is None:
+            ref = sums.clone()
         ms = float(np.mean(t))
         res[name] = {"ms_per_step": ms, "trees_per_s": world * 4096 * T / (ms / 1000.0),
-                     "nodes_per_s": world * B.N / (ms / 1000.0), "draws_per_step": int(draws)}
+                     "nodes_per_s": world * B.N / (ms / 1000.0), "draws_per_step": int(draws),
+                     "same_sums": bool(torch.equal(ref, sums))}
+    th, split, tile = B.schedule()
+    return {"graphs": 4096, "total_vertices": int(B.N), "trees_per_graph": T,
+            "schedule": {"threads": th, "warp_per_tree_up_to_n": split, "trees_per_item": tile},
+            "persistent_graph": res["persistent_graph"], "per_graph_launch": res["per_graph_launch"],
+            "speedup_vs_per_graph_launch": res["per_graph_launch"]["ms_per_step"] / res["persistent_graph"]["ms_per_step"],
+            "steps": steps, "warmup": warmup, "generation_s": gen_s, "autotune_s": tune_s}
+
+
+def run_batch(args, rwc, torch, dev, world, rank):
+    res = batch_measure(rwc, torch, dev, args.steps, args.warmup, world)
     if rank == 0:
         line = {"metric": METRIC, "value": res["persistent_graph"]["trees_per_s"], "unit": "trees/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": res["persistent_graph"]["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
-                "config": {"workload": "batch4096", "graphs": 4096, "total_vertices": int(B.N),
-                           "trees_per_graph": T},
-                "batch": res,
-                "speedup_vs_per_graph_launch": res["per_graph_launch"]["ms_per_step"] / res["persistent_graph"]["ms_per_step"]}
+                "config": {"workload": "batch4096", "graphs": 4096, "total_vertices": res["total_vertices"],
+                           "trees_per_graph": res["trees_per_graph"]},
+                "batch": res}
         print(json.dumps(line), flush=True)
+
+
+def rmat24_measure(rwc, torch, dev, hbm_peak, steps=2, warmup=1):
+    """The paper-size stand-in: R-MAT scale 24, lognormal(0, 1) weights
+    through the alias tables, int64 arc offsets, 500 trees per step, sampling
+    plus the pivot solve and recovery."""
+    key, T = "rmat24", WORKLOADS["rmat24"][0][1]
+    t0 = time.perf_counter()
+    g = make_graph(key)
+    gen_s = time.perf_counter() - t0
+    G = rwc.Graph.from_synth(g, flags=graph_flags(key, rwc))
+    sums = torch.zeros(g.n, dtype=torch.float64, device=dev)
+    opt = rwc.Options(profile=1)
+
+    def one():
+        sums.zero_()
+        st = rwc.rwc_sample_trees(G.handle, 1, 0, T, sums, None, None, opt)
+        return st, G.estimate(sums, T)
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    ms, sample_ms, draws = [], [], 0
+    H = None
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st, H = one()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        sample_ms.append(sum(st.phase_ms))
+        draws = st.draws
+    mre, T1 = rwc.rwc_predict_mre(G.handle, sums, T, H, target=0.01)
+    smp = float(np.mean(sample_ms))
+    alg = algorithmic_bytes(draws, T, g.n, True, True)
+    out = {"trees": T, "n": g.n, "arcs": g.nnz, "ms_per_step": float(np.mean(ms)),
+           "trees_per_s": T / (float(np.mean(ms)) / 1000.0), "sample_ms": smp,
+           "draws_per_tree": draws / T, "mre_pred": mre, "trees_for_1pct": int(T1),
+           "roofline": {"kernel": "w_trees", "achieved": alg / (smp / 1000.0) / 1e9, "peak": hbm_peak,
+                        "unit": "GB/s", "frac": alg / (smp / 1000.0) / 1e9 / hbm_peak,
+                        "unit_bytes": {"per_draw": bytes_per_draw(True, True),
+                                       "per_tree_vertex": BYTES_PER_TREE_VERTEX}},
+           "steps": steps, "warmup": warmup, "generation_s": gen_s}
+    del G, sums
+    torch.cuda.empty_cache()
+    return out
+
+
+def grad_measure(rwc, torch, dev, steps=3):
+    """rwc_grad on the 1e5-vertex random geometric graph (k = 64 sketch
+    columns, CG to 1e-8): milliseconds per call; and the sketch's error
+    against the exact gradient (k = 0, one solve per vertex) on the
+    2000-vertex graph of the same generator, where the exact one is cheap."""
+    import synth
+    g = synth.rgg(100_000, 12.0, seed=0, sigma=0.5)
+    G = rwc.Graph.from_synth(g)
+    c = torch.tensor(synth.uniform_vector(g.n, 1), dtype=torch.float64, device=dev)
+    G.grad(c, k=64, sketch_seed=77, tol=1e-8)
+    torch.cuda.synchronize()
+    t = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        G.grad(c, k=64, sketch_seed=77, tol=1e-8)
+        e1.record()
+        torch.cuda.synchronize()
+        t.append(e0.elapsed_time(e1))
+    g2 = synth.rgg(2000, 12.0, seed=0, sigma=0.5)
+    G2 = rwc.Graph.from_synth(g2)
+    c2 = torch.tensor(synth.uniform_vector(g2.n, 1), dtype=torch.float64, device=dev)
+    ex = G2.grad(c2, k=0, tol=1e-10).double()
+    errs = []
+    for sk_seed in range(8):
+        sk = G2.grad(c2, k=64, sketch_seed=sk_seed, tol=1e-10).double()
+        errs.append(((sk - ex).norm() / ex.norm()).item())
+    med_edge = float(((sk - ex).abs() / ex.abs().clamp_min(1e-300)).median().item())
+    return {"n": g.n, "edges": g.nnz // 2, "k": 64, "cg_tol": 1e-8, "ms_per_call": float(np.mean(t)),
+            "calls": steps,
+            "jl_error_k64": {"graph": "rgg n=2000 (same generator)", "rel_l2_mean_over_8_sketches": float(np.mean(errs)),
+                             "rel_l2_min": float(np.min(errs)), "rel_l2_max": float(np.max(errs)),
+                             "median_per_edge_rel": med_edge}}
 
 
 def main():
@@ -312,7 +448,12 @@ def main():
     ap.add_argument("--trees", type=int, default=0, help="override trees per graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--ref-budget", type=float, default=20.0)
+    ap.add_argument("--ref-budget", type=float, default=20.0, help="seconds of CPU baseline sampling")
+    ap.add_argument("--ref-trees", type=int, default=0, help="reference arm: trees per graph per step (0 = 2 per core)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the R-MAT 24, batch and gradient measurements added to the line")
+    ap.add_argument("--extras-budget", type=float, default=1200.0,
+                    help="wall seconds after which the remaining extra measurements are skipped")
     ap.add_argument("--walkers", type=int, default=0, help="walkers per tree (0 = auto)")
     ap.add_argument("--policy", type=int, default=0, help="walker conflict policy (0 default: 3 up to 64 walkers per tree, else 1; 1 yield and wait, 2 wait, 3 yield and take a fresh start)")
     ap.add_argument("--diag", action="store_true", help="count walker loop iterations per state (slower)")
@@ -363,7 +504,11 @@ def main():
         for key, T, g, G, sums in graphs:
             sums.zero_()
             st = rwc.rwc_sample_trees(G.handle, 1, tree_base, T, sums, None, None, opt)
-            H = G.estimate(sums, T)
+            if dist:
+                # the one exchange of the path: add the ranks' visit sums
+                # (exact integers), then estimate from all world * T trees
+                shard.all_reduce_sums(sums)
+            H = G.estimate(sums, world * T)
             Hs.append(H)
             if stats_out is not None:
                 stats_out.append((key, st.as_dict()))
@@ -406,42 +551,62 @@ def main():
     # library's stopping rule) and the trees it needs for 1%
     acc = {}
     for (key, T, g, G, sums), H in zip(graphs, Hs):
-        mre, T1 = rwc.rwc_predict_mre(G.handle, sums, T, H, target=0.01)
+        mre, T1 = rwc.rwc_predict_mre(G.handle, sums, world * T, H, target=0.01)
         acc[key] = {"mre_pred": mre, "trees_for_1pct": int(T1), "n": g.n,
-                    "draws_per_tree": float(sums.sum().item() / T)}
+                    "draws_per_tree": float(sums.sum().item() / (world * T))}
 
-    # per-kernel roofline from the profiled phases (timed region only)
+    # roofline of the sampler: the method's algorithmic bytes (per draw: row
+    # bounds + arc head [+ alias entry]; per tree and vertex: parent + visit
+    # count) over the device time of the sampler's kernels in the timed
+    # region; the dominant kernel takes all but a fraction of a percent of it
     phase_ms = {p: 0.0 for p in PHASE_NAMES}
-    phase_units = {p: 0 for p in PHASE_NAMES}
-    phase_launch = {p: 0 for p in PHASE_NAMES}
-    phase_bytes = {p: 0.0 for p in PHASE_NAMES}
-    sampler_ms = 0.0
+    per_graph = {}
+    alg_total, impl_total, traffic_total, sampler_ms, launches_dom = 0.0, 0.0, 0.0, 0.0, 0
+    traffic_known = True
     for key, st in all_stats:
-        g = [x for x in graphs if x[0] == key][0][2]
-        info = [x for x in graphs if x[0] == key][0][3].info
+        gi = [x for x in graphs if x[0] == key][0]
+        n, info = gi[2].n, gi[3].info
+        T_key = gi[1]
+        ms_k = sum(st["phase_ms"])
+        alg = algorithmic_bytes(st["draws"], T_key, n, bool(info.weighted), bool(info.offsets64))
+        impl = st["draws"] * IMPL_BYTES_PER_DRAW if st["mode"] == 3 else 0
+        tpd = traffic_per_draw(key) if st["mode"] == 3 else None
+        traffic_known &= tpd is not None
         for i, p in enumerate(PHASE_NAMES):
             phase_ms[p] += st["phase_ms"][i]
-            phase_units[p] += st["phase_units"][i]
-            phase_launch[p] += st["phase_launches"][i]
-            phase_bytes[p] += st["phase_units"][i] * bytes_per_unit(p, st["mode"], bool(info.weighted),
-                                                                    bool(info.offsets64))
-            sampler_ms += st["phase_ms"][i]
+        alg_total += alg
+        impl_total += impl
+        traffic_total += (tpd or 0.0) * st["draws"]
+        sampler_ms += ms_k
+        launches_dom += max(1, st["phase_launches"][1])
+        pg = per_graph.setdefault(key, {"alg_bytes": 0.0, "ms": 0.0, "draws": 0})
+        pg["alg_bytes"] += alg
+        pg["ms"] += ms_k
+        pg["draws"] += st["draws"]
     dom = max(PHASE_NAMES, key=lambda p: phase_ms[p])
     dom_mode = all_stats[-1][1]["mode"] if all_stats else 0
-    nl = max(1, phase_launch[dom])
-    per_launch_bytes = phase_bytes[dom] / nl
-    per_launch_s = phase_ms[dom] / 1000.0 / nl
-    achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
     kname = KERNEL_NAMES.get(dom_mode, {}).get(dom, dom)
-    traffic = traffic_for(args.workload, kname)
+    achieved = alg_total / (sampler_ms / 1000.0) / 1e9 if sampler_ms > 0 else 0.0
+    traffic = traffic_total / launches_dom if traffic_known and launches_dom else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic,
-                # DRAM bytes actually moved (ncu, per launch) over the live launch time
-                "dram_gbs": traffic / per_launch_s / 1e9 if traffic and per_launch_s > 0 else None,
-                "dram_frac": traffic / per_launch_s / 1e9 / hbm_peak if traffic and per_launch_s > 0 else None,
-                "algorithmic_bytes_per_launch": per_launch_bytes,
-                "kernel": KERNEL_NAMES.get(dom_mode, {}).get(dom, dom),
-                "unit_bytes": bytes_per_unit(dom, dom_mode, False, False),
+                "kernel": kname,
+                "algorithmic_bytes_per_launch": alg_total / max(1, launches_dom),
+                "launch_ms": sampler_ms / max(1, launches_dom),
+                "unit_bytes": {"per_draw": {k: bytes_per_draw(bool(G.info.weighted), bool(G.info.offsets64))
+                                            for k, _T, _g, G, _s in graphs},
+                               "per_tree_vertex": BYTES_PER_TREE_VERTEX},
+                # the walker's own state-word traffic, not part of `achieved`
+                "implementation_bytes_per_draw": IMPL_BYTES_PER_DRAW if dom_mode == 3 else 0,
+                "implementation_gbs": impl_total / (sampler_ms / 1000.0) / 1e9 if sampler_ms > 0 else 0.0,
+                # DRAM bytes actually moved (ncu per draw on a small case, scaled by the draws)
+                "dram_gbs": traffic_total / (sampler_ms / 1000.0) / 1e9 if traffic_known and sampler_ms > 0 else None,
+                "dram_frac": traffic_total / (sampler_ms / 1000.0) / 1e9 / hbm_peak if traffic_known and sampler_ms > 0 else None,
+                "traffic_source": {f: TRAFFIC_PER_DRAW[f][1] for f in {family(k) for k, *_ in graphs} if f in TRAFFIC_PER_DRAW},
+                "per_graph": {k: {"gbs": v["alg_bytes"] / (v["ms"] / 1000.0) / 1e9 if v["ms"] > 0 else 0.0,
+                                  "frac": v["alg_bytes"] / (v["ms"] / 1000.0) / 1e9 / hbm_peak if v["ms"] > 0 else 0.0,
+                                  "draws_per_s": v["draws"] / (v["ms"] / 1000.0) if v["ms"] > 0 else 0.0}
+                              for k, v in per_graph.items()},
                 "peak_source": f"{peak_src} hbm_gbs",
                 "phase_share": {p: phase_ms[p] / max(sampler_ms, 1e-9) for p in PHASE_NAMES}}
 
@@ -500,13 +665,30 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         built = {key: g for key, T, g, G, sums in graphs}
-        v, cores, samp = cpu_baseline(args.workload, graphs=built)
+        v, cores, samp = cpu_baseline(args.workload, budget_s=args.ref_budget, graphs=built)
         cpu = {"value": v, "unit": "trees/s", "cores": cores, "kind": "oracle", "sample": samp}
         try:   # the paper's setting, reported beside the all-core baseline
             v1, samp1 = cpu_single_thread(args.workload, graphs=built)
             cpu["single_thread"] = {"value": v1, "unit": "trees/s", "cores": 1, "sample": samp1}
         except Exception as exc:  # a failed extra measurement must not cost the line
             cpu["single_thread"] = {"error": str(exc)[:200]}
+
+    # further workloads measured in the same run (rank 0 at N = 1): the
+    # paper-size R-MAT 24, the 4096-graph batch and the gradient; each is
+    # skipped once the run has used its wall-time allowance
+    extras = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras = {}
+        for name, fn in (("rmat24", lambda: rmat24_measure(rwc, torch, dev, hbm_peak)),
+                         ("batch4096", lambda: batch_measure(rwc, torch, dev, steps=3, warmup=1)),
+                         ("grad_rgg100k", lambda: grad_measure(rwc, torch, dev))):
+            if time.perf_counter() - T_START > args.extras_budget:
+                extras[name] = {"skipped": f"run past {args.extras_budget:.0f} s of wall time"}
+                continue
+            try:
+                extras[name] = fn()
+            except Exception as exc:  # a failed extra must not cost the line
+                extras[name] = {"error": str(exc)[:300]}
 
     if rank == 0:
         line = {
@@ -522,6 +704,7 @@ def main():
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "extras": extras,
             "gpu_launches": int(launches),
             "clocks": clk,
             "wall_s_timed": t_wall,

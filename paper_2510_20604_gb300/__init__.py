@@ -14,7 +14,7 @@ from ._binding import (RWCError, Options, Stats, GraphInfo, lib, lib_path,
                        rwc_graph_destroy, rwc_sample_trees, rwc_sample_trees_noalloc,
                        rwc_estimate, rwc_recover,
                        rwc_solve, rwc_grad, rwc_batch_create, rwc_batch_sample,
-                       rwc_batch_roots, rwc_autotune, rwc_batch_destroy, rwc_mre, rwc_kendall, rwc_auto_params, Params, rwc_trap_walks, rwc_predict_mre,
+                       rwc_batch_roots, rwc_autotune, rwc_batch_get_schedule, rwc_batch_set_schedule, rwc_batch_destroy, rwc_mre, rwc_kendall, rwc_auto_params, Params, rwc_trap_walks, rwc_predict_mre,
                        MODE_AUTO, MODE_GLOBAL, MODE_SHARED, MODE_WALKER, GRAPH_INT64_OFFSETS,
                        GRAPH_SKIP_CONNECTIVITY)
 from .api import Graph, Batch, RWCFunction, fastwalk, fastwalk_to_target
@@ -25,6 +25,7 @@ __all__ = [
     "rwc_last_error", "rwc_graph_create", "rwc_graph_info", "rwc_graph_destroy",
     "rwc_sample_trees", "rwc_sample_trees_noalloc", "rwc_estimate", "rwc_recover", "rwc_solve", "rwc_grad",
     "rwc_batch_create", "rwc_batch_sample", "rwc_batch_roots", "rwc_autotune",
+    "rwc_batch_get_schedule", "rwc_batch_set_schedule",
     "rwc_batch_destroy", "rwc_mre", "rwc_kendall", "rwc_auto_params", "Params", "rwc_trap_walks", "rwc_predict_mre", "MODE_AUTO", "MODE_GLOBAL", "MODE_SHARED", "MODE_WALKER",
     "GRAPH_INT64_OFFSETS", "GRAPH_SKIP_CONNECTIVITY", "Graph", "Batch", "RWCFunction",
     "fastwalk", "fastwalk_to_target",

@@ -101,6 +101,8 @@ def lib():
         "rwc_batch_sample": ([_vp, _u64, _i64, _vp, _i32, _i32, ctypes.POINTER(Stats), _vp], _i32),
         "rwc_batch_roots": ([_vp, _vp], _i32),
         "rwc_autotune": ([_vp, ctypes.c_char_p, _vp], _i32),
+        "rwc_batch_get_schedule": ([_vp, _vp], _i32),
+        "rwc_batch_set_schedule": ([_vp, _i32, _i32, _i32], _i32),
         "rwc_batch_destroy": ([_vp], _i32),
         "rwc_mre": ([_i64, _vp, _vp, _vp, _vp], _i32),
         "rwc_auto_params": ([_vp, _d, _i32, _d, ctypes.POINTER(Params), _vp], _i32),
@@ -272,6 +274,17 @@ def rwc_batch_roots(b, G) -> np.ndarray:
 
 def rwc_autotune(b, cache_path=None, stream=None):
     _check(lib().rwc_autotune(b, cache_path.encode() if cache_path else None, _stream(stream)))
+
+
+def rwc_batch_get_schedule(b) -> tuple:
+    """(threads per block, split: largest n run warp-per-tree, trees per item)."""
+    out = np.zeros(3, np.int32)
+    _check(lib().rwc_batch_get_schedule(b, out.ctypes.data))
+    return tuple(int(x) for x in out)
+
+
+def rwc_batch_set_schedule(b, threads, split, tile):
+    _check(lib().rwc_batch_set_schedule(b, int(threads), int(split), int(tile)))
 
 
 def rwc_batch_destroy(b):

@@ -154,6 +154,13 @@ class Batch:
     def autotune(self, cache_path=None, stream=None):
         B.rwc_autotune(self.handle, cache_path, stream)
 
+    def schedule(self):
+        """(threads per block, split: largest n run warp-per-tree, trees per item)."""
+        return B.rwc_batch_get_schedule(self.handle)
+
+    def set_schedule(self, threads, split, tile):
+        B.rwc_batch_set_schedule(self.handle, threads, split, tile)
+
     def close(self):
         if getattr(self, "_ptr", None):
             B.rwc_batch_destroy(self._ptr)

@@ -1,8 +1,12 @@
 // Batched sampler: all trees of thousands of small graphs in one persistent
-// launch per size class, work items (graph, tile of trees) pulled from a
-// device counter (no grid-wide barrier); the launches of a call are captured
-// once into a CUDA graph and replayed.  Each tree runs in one thread block
-// with its state in shared memory (smem_tree.cuh).
+// launch.  Work items (graph, tile of trees) are pulled from device counters
+// (no grid-wide barrier).  Items of the larger graphs run block-per-tree; the
+// items of graphs with at most `split` vertices run warp-per-tree (every warp
+// of a block pulls its own items and keeps its tree in its own slice of the
+// block's shared memory), or block-per-tree as well when the schedule says so.
+// The autotuner times candidate schedules (block size, split, tile) on the
+// device; the launch of a call is captured once into a CUDA graph and
+// replayed.  Tree state lives in shared memory (smem_tree.cuh).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -28,50 +32,76 @@ struct BItem {
     int32_t tile;   // index of the tile of trees within the graph
 };
 
-constexpr int NCLASS = 2;
+// One work item: the tiles' trees of graph it.g, run by the group Grp whose
+// tree state is carved from `region`.  Adds the visit totals to sums.
+// Returns the group-uniform error mask.
+template <bool OFF64, bool W, class Grp>
+__device__ int run_item(const DevGraph &base, const BGraph *__restrict__ graphs, BItem it,
+                        unsigned char *region, int tile, int64_t T, uint32_t k0, uint32_t k1,
+                        int64_t max_rounds, double *sums, unsigned long long *round_ctr) {
+    const BGraph bg = graphs[it.g];
+    DevGraph g = base;
+    g.n = bg.n;
+    g.root = bg.root;
+    if (OFF64) g.rp64 = base.rp64 + bg.voff;
+    else g.rp32 = base.rp32 + bg.voff;
+    SmemTree S;
+    S.carve(region, bg.n);
+    for (int u = Grp::rank(); u < bg.n; u += Grp::size()) S.acc[u] = 0;
+    const int64_t t0 = (int64_t)it.tile * tile, t1 = std::min<int64_t>(T, t0 + tile);
+    int mask = 0;
+    unsigned long long rounds = 0;
+    for (int64_t t = t0; t < t1 && !mask; ++t) {
+        int64_t r = 0;
+        mask = smem_tree<OFF64, W, Grp>(g, S, (uint32_t)t, (uint32_t)it.g, k0, k1, max_rounds,
+                                        nullptr, nullptr, &r);
+        rounds += (unsigned long long)r;
+    }
+    Grp::sync();
+    if (mask) return mask;
+    unsigned long long draws = 0;
+    for (int u = Grp::rank(); u < bg.n; u += Grp::size()) {
+        draws += S.acc[u];
+        if (S.acc[u]) atomicAdd(sums + bg.voff + u, (double)S.acc[u]);
+    }
+    if (draws) atomicAdd(round_ctr + 1, draws);
+    if (Grp::rank() == 0 && rounds) atomicAdd(round_ctr, rounds);
+    return 0;
+}
 
+// Persistent kernel over both item lists: first every block pulls
+// block-per-tree items, then every warp pulls warp-per-tree items into its
+// own shared-memory slice of warp_slice bytes.
 template <bool OFF64, bool W>
 __global__ void b_persistent(DevGraph base, const BGraph *__restrict__ graphs,
-                             const BItem *__restrict__ items, int64_t nitems, int *next_item,
-                             int tile, int64_t T, uint32_t k0, uint32_t k1, int64_t max_rounds,
-                             double *sums, int *err, unsigned long long *round_ctr) {
+                             const BItem *__restrict__ bitems, int64_t nb,
+                             const BItem *__restrict__ witems, int64_t nw, int *next_item,
+                             int warp_slice, int tile, int64_t T, uint32_t k0, uint32_t k1,
+                             int64_t max_rounds, double *sums, int *err,
+                             unsigned long long *round_ctr) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int item;
-    unsigned long long rounds_here = 0;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) item = atomicAdd(next_item, 1);
         __syncthreads();
         const int i = item;
-        if (i >= nitems) break;
-        const BItem it = items[i];
-        const BGraph bg = graphs[it.g];
-        DevGraph g = base;
-        g.n = bg.n;
-        g.root = bg.root;
-        if (OFF64) g.rp64 = base.rp64 + bg.voff;
-        else g.rp32 = base.rp32 + bg.voff;
-        SmemTree S;
-        S.carve(smem, bg.n);
-        for (int u = threadIdx.x; u < bg.n; u += blockDim.x) S.acc[u] = 0;
-        const int64_t t0 = (int64_t)it.tile * tile, t1 = std::min<int64_t>(T, t0 + tile);
-        int mask = 0;
-        for (int64_t t = t0; t < t1 && !mask; ++t) {
-            int64_t r = 0;
-            mask = smem_tree<OFF64, W>(g, S, (uint32_t)t, (uint32_t)it.g, k0, k1, max_rounds,
-                                       nullptr, nullptr, &r);
-            rounds_here += (unsigned long long)r;
-        }
-        __syncthreads();
-        if (mask) { if (threadIdx.x == 0) atomicOr(err, mask); break; }
-        unsigned long long draws = 0;
-        for (int u = threadIdx.x; u < bg.n; u += blockDim.x) {
-            draws += S.acc[u];
-            if (S.acc[u]) atomicAdd(sums + bg.voff + u, (double)S.acc[u]);
-        }
-        if (draws) atomicAdd(round_ctr + 1, draws);
+        if (i >= nb) break;
+        const int mask = run_item<OFF64, W, BlockGroup>(base, graphs, bitems[i], smem, tile, T, k0, k1,
+                                                        max_rounds, sums, round_ctr);
+        if (mask) { if (threadIdx.x == 0) atomicOr(err, mask); return; }
     }
-    if (threadIdx.x == 0 && rounds_here) atomicAdd(round_ctr, rounds_here);
+    if (nw == 0) return;
+    unsigned char *region = smem + (size_t)(threadIdx.x >> 5) * warp_slice;
+    for (;;) {
+        int i = 0;
+        if ((threadIdx.x & 31) == 0) i = atomicAdd(next_item + 1, 1);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= nw) break;
+        const int mask = run_item<OFF64, W, WarpGroup>(base, graphs, witems[i], region, tile, T, k0, k1,
+                                                       max_rounds, sums, round_ctr);
+        if (mask) { if ((threadIdx.x & 31) == 0) atomicOr(err, mask); return; }
+    }
 }
 
 template <class F>
@@ -98,16 +128,17 @@ struct rwc_batch {
     std::vector<int32_t> roots;
     DevGraph base;                     // concatenated CSR (local column ids)
     BGraph *graphs = nullptr;
-    // size classes: [0] n <= class_split, [1] the rest
-    int class_split = 2048;
-    int threads[NCLASS] = {256, 512};
+    // schedule: block size, the largest n run warp-per-tree (0: none), trees
+    // per work item
+    int threads = 256;
+    int split = 1024;
     int tile = 4;
-    int max_n[NCLASS] = {0, 0};
-    BItem *items[NCLASS] = {nullptr, nullptr};
-    int64_t nitems[NCLASS] = {0, 0};
+    int max_n[2] = {0, 0};             // largest n of the block / warp item lists
+    BItem *items[2] = {nullptr, nullptr};
+    int64_t nitems[2] = {0, 0};
     int64_t items_T = -1;              // T the item lists were built for
-    int64_t items_tile = -1;
-    void *scratch = nullptr;           // [0] err, [8] rounds, [16] draws, [32..96) item counters
+    int64_t items_tile = -1, items_split = -1;
+    void *scratch = nullptr;           // [0] err, [8] rounds, [16] draws, [32..40) item counters
     std::vector<void *> allocs;
     // captured launches
     cudaGraph_t graph = nullptr;
@@ -135,25 +166,33 @@ void drop_graph(rwc_batch *b) {
     b->cap_T = -1;
 }
 
-// Work items of each size class for T trees per graph, largest graphs first.
+// Bytes of one warp's shared-memory slice for trees of up to n vertices.
+size_t warp_slice_bytes(int n) { return (smem_tree_bytes(n) + 15) & ~(size_t)15; }
+
+// Dynamic shared memory of the persistent kernel for the current schedule.
+size_t batch_smem(const rwc_batch *b) {
+    size_t s = b->nitems[0] ? smem_tree_bytes(b->max_n[0]) : 0;
+    if (b->nitems[1]) s = std::max(s, (size_t)(b->threads / 32) * warp_slice_bytes(b->max_n[1]));
+    return std::max<size_t>(s, 64);
+}
+
+// Work items for T trees per graph: list 0 (block-per-tree) holds graphs with
+// more than `split` vertices, list 1 (warp-per-tree) the others; each list
+// runs its largest graphs first.
 rwc_status build_items(rwc_batch *b, int64_t T) {
-    if (b->items_T == T && b->items_tile == b->tile) return RWC_OK;
-    for (int c = 0; c < NCLASS; ++c) {
+    if (b->items_T == T && b->items_tile == b->tile && b->items_split == b->split) return RWC_OK;
+    for (int c = 0; c < 2; ++c) {
         std::vector<BItem> v;
         std::vector<int32_t> order;
         for (int32_t g = 0; g < b->G; ++g) {
-            const int cls = b->hgraphs[g].n <= b->class_split ? 0 : 1;
+            const int cls = b->hgraphs[g].n <= b->split ? 1 : 0;
             if (cls == c) order.push_back(g);
         }
         std::stable_sort(order.begin(), order.end(),
                          [&](int32_t x, int32_t y) { return b->hgraphs[x].n > b->hgraphs[y].n; });
         const int64_t ntile = (T + b->tile - 1) / b->tile;
-        for (int64_t t = 0; t < ntile; ++t)
-            for (int32_t g : order) v.push_back(BItem{g, (int32_t)t});
-        // largest graphs' tiles first overall
-        std::stable_sort(v.begin(), v.end(), [&](const BItem &x, const BItem &y) {
-            return b->hgraphs[x.g].n > b->hgraphs[y.g].n;
-        });
+        for (int32_t g : order)
+            for (int64_t t = 0; t < ntile; ++t) v.push_back(BItem{g, (int32_t)t});
         if (b->items[c]) { cudaFree(b->items[c]); b->allocs.erase(std::find(b->allocs.begin(), b->allocs.end(), (void *)b->items[c])); }
         b->items[c] = nullptr;
         b->nitems[c] = (int64_t)v.size();
@@ -166,35 +205,37 @@ rwc_status build_items(rwc_batch *b, int64_t T) {
     }
     b->items_T = T;
     b->items_tile = b->tile;
+    b->items_split = b->split;
     drop_graph(b);
     return RWC_OK;
 }
 
-// Enqueue the persistent launches of one call.
+// Enqueue the persistent launch of one call.
 rwc_status enqueue(rwc_batch *b, uint64_t seed, int64_t T, double *sums, cudaStream_t st) {
     int *err = (int *)b->scratch;
     unsigned long long *rounds = (unsigned long long *)((char *)b->scratch + 8);
     int *counters = (int *)((char *)b->scratch + 32);
-    RWC_CUDA_TRY(cudaMemsetAsync((char *)b->scratch + 32, 0, 64, st));
+    RWC_CUDA_TRY(cudaMemsetAsync((char *)b->scratch + 32, 0, 8, st));
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const size_t smem = batch_smem(b);
+    if (smem > 227 * 1024) return set_error(RWC_ERR_UNSUPPORTED, "batch schedule needs %zu bytes of shared memory", smem);
     rwc_status status = RWC_OK;
-    for (int c = 0; c < NCLASS; ++c) {
-        if (!b->nitems[c]) continue;
-        const size_t smem = smem_tree_bytes(b->max_n[c]);
-        dispatch(b->off64, b->weighted, [&](auto o64, auto wt) {
-            auto kern = b_persistent<decltype(o64)::value, decltype(wt)::value>;
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            int per_sm = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, b->threads[c], smem);
-            if (per_sm < 1) { status = set_error(RWC_ERR_UNSUPPORTED, "batch class %d does not fit on an SM", c); return; }
-            const int64_t blocks = std::min<int64_t>(b->nitems[c], (int64_t)num_sms() * per_sm);
-            ::rwc::count_launches(1); kern<<<(unsigned)blocks, b->threads[c], smem, st>>>(
-                b->base, b->graphs, b->items[c], b->nitems[c], counters + c, b->tile, T, k0, k1,
-                (int64_t)1 << 22, sums, err, rounds);
-        });
-        RWC_TRY(status);
-        RWC_CUDA_TRY(cudaGetLastError());
-    }
+    dispatch(b->off64, b->weighted, [&](auto o64, auto wt) {
+        auto kern = b_persistent<decltype(o64)::value, decltype(wt)::value>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, b->threads, smem);
+        if (per_sm < 1) { status = set_error(RWC_ERR_UNSUPPORTED, "batch block does not fit on an SM"); return; }
+        const int64_t warps = b->threads / 32;
+        const int64_t want = std::max<int64_t>(b->nitems[0], (b->nitems[1] + warps - 1) / warps);
+        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * per_sm));
+        ::rwc::count_launches(1);
+        kern<<<(unsigned)blocks, b->threads, smem, st>>>(
+            b->base, b->graphs, b->items[0], b->nitems[0], b->items[1], b->nitems[1], counters,
+            (int)warp_slice_bytes(b->max_n[1]), b->tile, T, k0, k1, (int64_t)1 << 22, sums, err, rounds);
+    });
+    RWC_TRY(status);
+    RWC_CUDA_TRY(cudaGetLastError());
     return RWC_OK;
 }
 
@@ -212,6 +253,7 @@ rwc_status finish(rwc_batch *b, rwc_stats_t *stats, int mode, int64_t T, cudaStr
         stats->marked = b->host[2];
         stats->chunks = 1;
         stats->mode = mode;
+        stats->block_threads = mode == 3 ? 0 : b->threads;
     }
     return RWC_OK;
 }
@@ -334,7 +376,7 @@ extern "C" rwc_status rwc_batch_sample(rwc_batch_t *b, uint64_t seed, int64_t T,
             DevGraph dg = b->base;
             dg.n = bg.n; dg.root = bg.root;
             if (b->off64) dg.rp64 = b->base.rp64 + bg.voff; else dg.rp32 = b->base.rp32 + bg.voff;
-            const int thr = bg.n <= b->class_split ? b->threads[0] : b->threads[1];
+            const int thr = bg.n <= 2048 ? 256 : 512;   // the block sizes of a plain per-graph launch
             const size_t smem = smem_tree_bytes(bg.n);
             rwc_status status = RWC_OK;
             dispatch(b->off64, b->weighted, [&](auto o64, auto wt) {
@@ -383,6 +425,38 @@ extern "C" rwc_status rwc_batch_sample(rwc_batch_t *b, uint64_t seed, int64_t T,
     return finish(b, stats, 5, T, st);
 }
 
+namespace {
+// Checks a schedule against the batch's graphs; the item lists must be built.
+bool schedule_fits(const rwc_batch *b) { return batch_smem(b) <= 227 * 1024; }
+}  // namespace
+
+extern "C" rwc_status rwc_batch_get_schedule(const rwc_batch_t *b, int32_t *host_sched) {
+    clear_error();
+    if (!b || !host_sched) return set_error(RWC_ERR_INVALID, "bad argument");
+    host_sched[0] = b->threads;
+    host_sched[1] = b->split;
+    host_sched[2] = b->tile;
+    return RWC_OK;
+}
+
+extern "C" rwc_status rwc_batch_set_schedule(rwc_batch_t *b, int32_t threads, int32_t split, int32_t tile) {
+    clear_error();
+    if (!b || threads < 32 || threads > 1024 || threads % 32 || split < 0 || split > 20000 || tile < 1)
+        return set_error(RWC_ERR_INVALID, "schedule needs threads in [32, 1024] (a multiple of 32), "
+                                          "0 <= split <= 20000 and tile >= 1");
+    int wmax = 0, bmax = 0;
+    for (const BGraph &g : b->hgraphs) (g.n <= split ? wmax : bmax) = std::max(g.n <= split ? wmax : bmax, g.n);
+    const size_t need = std::max(bmax ? smem_tree_bytes(bmax) : 0, wmax ? (size_t)(threads / 32) * warp_slice_bytes(wmax) : 0);
+    if (need > 227 * 1024)
+        return set_error(RWC_ERR_UNSUPPORTED, "schedule needs %zu bytes of shared memory per block", need);
+    b->threads = threads;
+    b->split = split;
+    b->tile = tile;
+    b->items_T = -1;
+    drop_graph(b);
+    return RWC_OK;
+}
+
 extern "C" rwc_status rwc_autotune(rwc_batch_t *b, const char *cache_path, rwc_stream_t stream) {
     clear_error();
     if (!b) return set_error(RWC_ERR_INVALID, "bad argument");
@@ -398,58 +472,58 @@ extern "C" rwc_status rwc_autotune(rwc_batch_t *b, const char *cache_path, rwc_s
             buf[len] = 0;
             const char *p = strstr(buf, sig);
             const char *colon = p ? strchr(p, ':') : nullptr;
-            int t0, t1, tl, cs;
-            if (colon && sscanf(colon + 1, " [%d, %d, %d, %d]", &t0, &t1, &tl, &cs) == 4) {
-                b->threads[0] = t0; b->threads[1] = t1; b->tile = tl; b->class_split = cs;
-                b->items_T = -1;
+            int th, sp, tl;
+            if (colon && sscanf(colon + 1, " [%d, %d, %d]", &th, &sp, &tl) == 3 &&
+                rwc_batch_set_schedule(b, th, sp, tl) == RWC_OK)
                 return RWC_OK;
-            }
+            clear_error();
         }
     }
     double *sums = nullptr;
     RWC_CUDA_TRY(cudaMallocAsync((void **)&sums, b->N * sizeof(double), st));
-    const int cand0[] = {128, 256, 512};
-    const int cand1[] = {256, 512, 1024};
-    const int tiles[] = {1, 4, 16};
-    const int splits[] = {1024, 2048, 4096};
+    // block size x the largest n run warp-per-tree (0: every tree block-per-tree)
+    // x trees per work item, each timed on 16 trees per graph
+    const int cand_threads[] = {128, 256, 512};
+    const int cand_split[] = {0, 512, 1024, 2048};
+    const int cand_tile[] = {1, 4, 16};
     const int64_t Tp = 16;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int bt0 = b->threads[0], bt1 = b->threads[1], btl = b->tile, bcs = b->class_split;
+    int bth = b->threads, bsp = b->split, btl = b->tile;
     rwc_status status = RWC_OK;
-    for (int cs : splits)
-        for (int t0 : cand0)
-            for (int t1 : cand1)
-                for (int tl : tiles) {
-                    b->threads[0] = t0; b->threads[1] = t1; b->tile = tl; b->class_split = cs;
-                    b->items_T = -1;
-                    if ((status = build_items(b, Tp)) != RWC_OK) goto done;
-                    cudaMemsetAsync(b->scratch, 0, 32, st);
-                    if ((status = enqueue(b, 12345, Tp, sums, st)) != RWC_OK) { status = RWC_OK; continue; }
-                    cudaEventRecord(e0, st);
-                    cudaMemsetAsync(b->scratch, 0, 32, st);
-                    if ((status = enqueue(b, 12346, Tp, sums, st)) != RWC_OK) { status = RWC_OK; continue; }
-                    cudaEventRecord(e1, st);
-                    cudaEventSynchronize(e1);
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    if (ms < best) { best = ms; bt0 = t0; bt1 = t1; btl = tl; bcs = cs; }
-                }
+    for (int sp : cand_split)
+        for (int th : cand_threads)
+            for (int tl : cand_tile) {
+                b->threads = th; b->split = sp; b->tile = tl;
+                b->items_T = -1;
+                if ((status = build_items(b, Tp)) != RWC_OK) goto done;
+                if (!schedule_fits(b)) continue;
+                cudaMemsetAsync(b->scratch, 0, 32, st);
+                if (enqueue(b, 12345, Tp, sums, st) != RWC_OK) { clear_error(); continue; }
+                cudaEventRecord(e0, st);
+                cudaMemsetAsync(b->scratch, 0, 32, st);
+                if (enqueue(b, 12346, Tp, sums, st) != RWC_OK) { clear_error(); continue; }
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) { best = ms; bth = th; bsp = sp; btl = tl; }
+            }
 done:
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFreeAsync(sums, st);
     RWC_CUDA_TRY(cudaStreamSynchronize(st));
     RWC_TRY(status);
-    b->threads[0] = bt0; b->threads[1] = bt1; b->tile = btl; b->class_split = bcs;
+    b->threads = bth; b->split = bsp; b->tile = btl;
     b->items_T = -1;
     drop_graph(b);
     if (cache_path) {
         FILE *f = fopen(cache_path, "w");
         if (f) {
-            fprintf(f, "{\"%s\": [%d, %d, %d, %d]}\n", sig, bt0, bt1, btl, bcs);
+            fprintf(f, "{\"%s\": [%d, %d, %d]}\n", sig, bth, bsp, btl);
             fclose(f);
         }
     }

@@ -32,10 +32,26 @@ struct SmemTree {
     }
 };
 
+// The thread group that runs one tree: a whole thread block, or one warp
+// (warp-per-tree, for small graphs: several trees per block, synchronised
+// with __syncwarp instead of block barriers).
+struct BlockGroup {
+    static __device__ __forceinline__ int rank() { return threadIdx.x; }
+    static __device__ __forceinline__ int size() { return blockDim.x; }
+    static __device__ __forceinline__ void sync() { __syncthreads(); }
+    static __device__ __forceinline__ int any(int p) { return __syncthreads_or(p); }
+};
+struct WarpGroup {
+    static __device__ __forceinline__ int rank() { return threadIdx.x & 31; }
+    static __device__ __forceinline__ int size() { return 32; }
+    static __device__ __forceinline__ void sync() { __syncwarp(); }
+    static __device__ __forceinline__ int any(int p) { return __any_sync(0xffffffffu, p); }
+};
+
 // Runs one tree; adds visits to S.acc; optionally writes the tree's parents
-// and visits rows.  Must be called by every thread of the block.  Returns a
-// block-uniform error mask (0 on success); *rounds gets the round count.
-template <bool OFF64, bool W>
+// and visits rows.  Must be called by every thread of the group.  Returns a
+// group-uniform error mask (0 on success); *rounds gets the round count.
+template <bool OFF64, bool W, class Grp = BlockGroup>
 __device__ int smem_tree(const DevGraph &g, const SmemTree &S, uint32_t tree, uint32_t gid,
                          uint32_t k0, uint32_t k1, int64_t max_rounds, int32_t *par_row,
                          int32_t *vis_row, int64_t *rounds) {
@@ -45,19 +61,19 @@ __device__ int smem_tree(const DevGraph &g, const SmemTree &S, uint32_t tree, ui
     uint16_t *K = S.K;
     int16_t *NM = S.NM;
     uint8_t *F = S.F;
-    __syncthreads();
-    for (int u = threadIdx.x; u < n; u += blockDim.x) {
+    Grp::sync();
+    for (int u = Grp::rank(); u < n; u += Grp::size()) {
         K[u] = 0;
         if (u == root) { F[u] = SF_SET; P[u] = -1; }
         else { F[u] = SF_MARK; P[u] = (int16_t)succ<OFF64, W>(g, u, 0u, tree, gid, k0, k1); }
     }
-    __syncthreads();
+    Grp::sync();
     int any = 1, bad = 0, lerr = 0;
     int64_t r = 0;
     while (any) {
         if (++r > max_rounds) { lerr |= SM_ERR_ROUNDS; bad = 1; break; }
         // walk to the next marked or settled vertex
-        for (int u = threadIdx.x; u < n; u += blockDim.x) {
+        for (int u = Grp::rank(); u < n; u += Grp::size()) {
             if (!(F[u] & SF_MARK)) continue;
             int x = P[u];
             for (int q = 0; !(F[x] & (SF_MARK | SF_SET)); ++q) {
@@ -66,9 +82,9 @@ __device__ int smem_tree(const DevGraph &g, const SmemTree &S, uint32_t tree, ui
             }
             NM[u] = (F[x] & SF_SET) ? (int16_t)-1 : (int16_t)x;
         }
-        __syncthreads();
+        Grp::sync();
         // classify: leader (smallest vertex of its cycle), reaches root, other
-        for (int u = threadIdx.x; u < n; u += blockDim.x) {
+        for (int u = Grp::rank(); u < n; u += Grp::size()) {
             if (!(F[u] & SF_MARK)) continue;
             int x = NM[u], saved = -3, power = 1, lam = 0;
             uint8_t c = 0;
@@ -82,9 +98,9 @@ __device__ int smem_tree(const DevGraph &g, const SmemTree &S, uint32_t tree, ui
             }
             F[u] |= c;
         }
-        __syncthreads();
+        Grp::sync();
         // pop cycles / settle segments that reach the root
-        for (int u = threadIdx.x; u < n; u += blockDim.x) {
+        for (int u = Grp::rank(); u < n; u += Grp::size()) {
             const uint8_t f = F[u];
             if (f & SF_LEAD) {
                 int w = u, q = 0;
@@ -107,23 +123,23 @@ __device__ int smem_tree(const DevGraph &g, const SmemTree &S, uint32_t tree, ui
                 } while (!(F[y] & (SF_MARK | SF_SET)));
             }
         }
-        __syncthreads();
+        Grp::sync();
         // popped vertices form the next marked set
         int mine = 0;
-        for (int u = threadIdx.x; u < n; u += blockDim.x) {
+        for (int u = Grp::rank(); u < n; u += Grp::size()) {
             const uint8_t f = F[u];
             const uint8_t nf = (uint8_t)((f & SF_SET) | ((f & SF_NEXT) ? SF_MARK : 0));
             F[u] = nf;
             mine |= (nf & SF_MARK);
         }
-        any = __syncthreads_or(mine);
-        bad = __syncthreads_or(lerr);
+        any = Grp::any(mine);
+        bad = Grp::any(lerr);
         if (bad) break;
     }
-    const int berr = __syncthreads_or(lerr) ? 1 : 0;
+    const int berr = Grp::any(lerr) ? 1 : 0;
     *rounds = r;
     if (!berr) {
-        for (int u = threadIdx.x; u < n; u += blockDim.x) {
+        for (int u = Grp::rank(); u < n; u += Grp::size()) {
             const uint32_t vis = (u == root) ? 0u : (uint32_t)K[u] + 1u;
             S.acc[u] += vis;
             if (par_row) par_row[u] = (u == root) ? -1 : (int32_t)P[u];
@@ -133,7 +149,7 @@ __device__ int smem_tree(const DevGraph &g, const SmemTree &S, uint32_t tree, ui
     // error mask, identical in every thread: OR of lerr over the block
     int mask = 0;
     for (int bit = 1; bit <= 4; bit <<= 1)
-        if (__syncthreads_or(lerr & bit)) mask |= bit;
+        if (Grp::any(lerr & bit)) mask |= bit;
     return mask;
 }
 

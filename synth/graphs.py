@@ -73,7 +73,11 @@ def from_edges(n: int, u, v, w=None, name: str = "", meta=None) -> Graph:
     a = np.minimum(u, v)
     b = np.maximum(u, v)
     key = a * n + b
-    _, first = np.unique(key, return_index=True)
+    # first copy of every key (a stable sort keeps input order among equals),
+    # then back into input order
+    order = np.argsort(key, kind="stable")
+    ks = key[order]
+    first = order[np.concatenate(([True], ks[1:] != ks[:-1]))] if len(ks) else order
     first.sort()
     a, b = a[first], b[first]
     if w is not None:
@@ -165,19 +169,24 @@ def rmat(scale: int, ef: int = 16, seed: int = 0, a=0.57, b=0.19, c=0.19,
         k = min(chunk, nsamp - s0)
         uu = np.zeros(k, dtype=np.int64)
         vv = np.zeros(k, dtype=np.int64)
+        # level lvl's draws for the chunk's k samples (one call draws the
+        # same stream as `scale` calls of k)
+        rr = rng.integers(0, 2 ** 32, size=(scale, k), dtype=np.uint64)
         for lvl in range(scale):
-            r = rng.integers(0, 2 ** 32, size=k, dtype=np.uint64)
+            r = rr[lvl]
             row_bit = r >= tb                      # quadrants c, d
             col_bit = ((r >= ta) & (r < tb)) | (r >= tc)   # quadrants b, d
-            bit = np.int64(1) << np.int64(scale - 1 - lvl)
-            uu |= np.where(row_bit, bit, 0)
-            vv |= np.where(col_bit, bit, 0)
+            sh = np.int64(scale - 1 - lvl)
+            uu |= row_bit.astype(np.int64) << sh
+            vv |= col_bit.astype(np.int64) << sh
+        del rr
         us.append(uu); vs.append(vv)
     u = np.concatenate(us); v = np.concatenate(vs)
     keep = u != v
     u, v = u[keep], v[keep]
     lo, hi = np.minimum(u, v), np.maximum(u, v)
-    key = np.unique(lo * n + hi)
+    key = np.sort(lo * n + hi)
+    key = key[np.concatenate(([True], key[1:] != key[:-1]))] if len(key) else key
     u, v = key // n, key % n
     w = _weights(rng, len(u), sigma)
     if with_path:

@@ -21,7 +21,7 @@ def _bench():
 
 def test_reference_arm_prints_one_json_line():
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "ba2000",
-                        "--steps", "1", "--warmup", "0", "--ref-budget", "0.5"],
+                        "--steps", "2", "--warmup", "0", "--ref-trees", "4"],
                        cwd=ROOT, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
@@ -31,6 +31,7 @@ def test_reference_arm_prints_one_json_line():
     assert d["higher_is_better"] is True and d["config"]["workload"] == "ba2000"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert d["steps"] == 2 and d["ms_per_step"] > 0
 
 
 def test_code_hash_ignores_comment_lines_only(tmp_path):
@@ -44,15 +45,27 @@ def test_code_hash_ignores_comment_lines_only(tmp_path):
     assert b.code_hash(str(p)) != h0
 
 
-def test_traffic_is_reported_only_for_the_measured_code():
+def test_traffic_is_reported_only_for_the_measured_code(tmp_path, monkeypatch):
     b = _bench()
-    key = ("grid1024+rmat20", "w_trees")
-    assert key in b.TRAFFIC
-    nbytes, src, sha = b.TRAFFIC[key]
-    assert nbytes > 0
+    src = "walker.cu"
     cur = b.code_hash(os.path.join(ROOT, "paper_2510_20604_gb300", "csrc", src))
-    assert b.traffic_for(*key) == (nbytes if cur == sha else None)
-    assert b.traffic_for("no-such-workload", "w_trees") is None
+    monkeypatch.setitem(b.TRAFFIC_PER_DRAW, "grid", (250.0, "grid 256x256", src, cur))
+    monkeypatch.setitem(b.TRAFFIC_PER_DRAW, "rmat", (99.0, "R-MAT 18", src, "0" * 64))
+    assert b.traffic_per_draw("grid1024") == 250.0
+    assert b.traffic_per_draw("rmat20") is None          # measured on other code
+    assert b.traffic_per_draw("ba2000") is None          # never measured
+    for fam, (nbytes, case, s, sha) in b.TRAFFIC_PER_DRAW.items():
+        assert nbytes > 0 and case and s.endswith(".cu") and len(sha) == 64
+
+
+def test_algorithmic_bytes():
+    b = _bench()
+    assert b.bytes_per_draw(False, False) == 12
+    assert b.bytes_per_draw(True, False) == 20
+    assert b.bytes_per_draw(True, True) == 28
+    # grid 1024^2 at 2000 trees with 42.56e9 draws: 527.5 GB
+    got = b.algorithmic_bytes(42.56e9, 2000, 1 << 20, False, False)
+    assert abs(got - (42.56e9 * 12 + 2000 * (1 << 20) * 8)) < 1
 
 
 def test_graph_flags():

@@ -36,10 +36,42 @@ def test_batch_matches_oracle_and_modes_agree():
     assert st.trees == T * len(gs)
 
 
+@pytest.mark.parametrize("sched", [(256, 0, 4), (256, 1024, 4), (128, 3000, 2), (512, 600, 1)])
+def test_batch_schedules_match_oracle(sched):
+    """Block-per-tree only, a warp-per-tree share of the small graphs, every
+    graph warp-per-tree, and a wide block with one tree per item: each
+    schedule gives every member exactly the oracle's sums."""
+    gs = _graphs(G=20, seed=13, nmax=3000)
+    B = rwc.Batch(gs)
+    B.set_schedule(*sched)
+    assert B.schedule() == sched
+    T = 9
+    s, st = B.sample(T, seed=2, use_graph=1)
+    assert st.block_threads == sched[0]
+    sums = s.cpu().numpy()
+    roots = B.roots()
+    o = B.offsets
+    for i, g in enumerate(gs):
+        ref = ow.Sampler(g, root=int(roots[i]), seed=2, graph_id=i).sample(0, T)
+        assert np.array_equal(sums[o[i]:o[i + 1]], ref["sums"]), (sched, i)
+
+
+def test_batch_schedule_rejects_oversized_slices():
+    gs = _graphs(G=6, seed=3, nmax=20000)
+    B = rwc.Batch(gs)
+    with pytest.raises(rwc.RWCError) as e:
+        B.set_schedule(1024, 20000, 1)      # 32 warps x 11 n bytes of shared memory
+    assert e.value.status in (1, 6)
+    with pytest.raises(rwc.RWCError):
+        B.set_schedule(100, 0, 1)           # not a multiple of 32
+
+
 def test_batch_autotune_and_large_graphs():
     gs = _graphs(G=10, seed=9, nmax=20000)
     B = rwc.Batch(gs)
     B.autotune(None)
+    th, split, tile = B.schedule()
+    assert th % 32 == 0 and tile >= 1 and split in (0, 512, 1024, 2048)
     T = 5
     s, _ = B.sample(T, seed=1)
     sums = s.cpu().numpy()
