@@ -50,7 +50,10 @@ WORKLOADS = {
     "rmat18": [("rmat18", 512)],
     "batch4096": [("batch4096", 256)],
     "rmat24": [("rmat24", 500)],
+    # accuracy sweep (not a throughput workload): eps in EPS_SWEEP
+    "eps-sweep": [("ba2000", 0)],
 }
+EPS_SWEEP = (0.3, 0.2, 0.1, 0.05, 0.02, 0.01)
 
 PHASE_NAMES = ("init", "walk", "classify", "pop", "finish", "accum")
 KERNEL_NAMES = {1: {"init": "g_init", "walk": "g_walk", "pop": "g_pop", "accum": "g_accum"},
@@ -438,6 +441,76 @@ def grad_measure(rwc, torch, dev, steps=3):
                              "median_per_edge_rel": med_edge}}
 
 
+def run_eps_sweep(args, rwc, torch, dev, rank):
+    """Runtime, error and ranking quality against the accuracy target eps
+    (the paper's Section 6 sweep over eps in [0.01, 0.3], on synthetic
+    stand-ins).  The tree-count lemma's l is a worst-case bound (about 3e8
+    trees at eps = 0.3 on BA-2000), so each eps gets the trees the variance
+    law of the visit counts predicts for a mean relative error of eps
+    (fastwalk_to_target).  BA n = 2000: measured MRE and Kendall distance
+    against a ground truth of 4e6 trees (predicted MRE ~0.02%; the paper uses
+    FastWalk at eps = 1e-4 the same way where no exact solve is possible).
+    Grid 512^2 and R-MAT 18: trees and runtime per eps, measured while the
+    tree count stays at most 4096, else from the per-tree time of that run."""
+    import synth
+    res = {}
+    g = synth.ba(2000, 3, seed=0)
+    G = rwc.Graph.from_synth(g)
+    T_gt = 4_000_000
+    t0 = time.perf_counter()
+    Hgt, _ = rwc.fastwalk(G, T_gt, seed=777)
+    torch.cuda.synchronize()
+    gt_s = time.perf_counter() - t0
+    rows = []
+    for eps in EPS_SWEEP:
+        rwc.fastwalk_to_target(G, eps, seed=1)      # warm-up of the same call
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        H, T, mre_pred = rwc.fastwalk_to_target(G, eps, seed=1)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        mre = float(rwc.rwc_mre(Hgt, H).item())
+        tau, _ = rwc.rwc_kendall(H, Hgt)
+        rows.append({"eps": eps, "trees": int(T), "seconds": dt, "mre_measured": mre,
+                     "mre_predicted": float(mre_pred), "kendall": tau})
+    res["ba2000"] = {"ground_truth_trees": T_gt, "ground_truth_s": gt_s, "rows": rows}
+    for key in ("grid512", "rmat18"):
+        gk = make_graph(key)
+        Gk = rwc.Graph.from_synth(gk)
+        T0 = 256
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sums, st, _, _ = Gk.sample(T0, seed=1, opt=rwc.Options(profile=1))
+        Hk = Gk.estimate(sums, T0)
+        torch.cuda.synchronize()
+        base_s = time.perf_counter() - t0
+        per_tree_s = sum(st.phase_ms) / 1000.0 / T0
+        solve_s = max(0.0, base_s - per_tree_s * T0)
+        mre0, _ = rwc.rwc_predict_mre(Gk.handle, sums, T0, Hk, target=0.01)
+        krow = []
+        for eps in EPS_SWEEP:
+            need = max(1, int(np.ceil(T0 * (mre0 / eps) ** 2)))
+            if need <= 4096:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                H, T, mp = rwc.fastwalk_to_target(Gk, eps, first_trees=need, seed=1)
+                torch.cuda.synchronize()
+                krow.append({"eps": eps, "trees": int(T), "seconds": time.perf_counter() - t0,
+                             "mre_predicted": float(mp), "measured": True})
+            else:
+                krow.append({"eps": eps, "trees": need, "seconds": need * per_tree_s + solve_s,
+                             "mre_predicted": eps, "measured": False})
+        res[key] = {"pilot_trees": T0, "pilot_mre_predicted": float(mre0), "rows": krow}
+        del Gk
+    if rank == 0:
+        line = {"metric": "RWC mean relative error, Kendall distance and runtime against eps",
+                "value": rows[-1]["seconds"], "unit": "s at eps=0.01 (BA n=2000)", "n_gpus": 1,
+                "steps": 1, "warmup": 1, "higher_is_better": False, "dtype": "int32/f64",
+                "data": "synthetic", "config": {"workload": "eps-sweep", "eps": list(EPS_SWEEP)},
+                "sweep": res}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -480,6 +553,9 @@ def main():
     dev = torch.device("cuda", local)
     hbm_peak, peak_src = load_peaks()
 
+    if args.workload == "eps-sweep":
+        run_eps_sweep(args, rwc, torch, dev, rank)
+        return
     if args.workload == "batch4096":
         run_batch(args, rwc, torch, dev, world, rank)
         if dist:

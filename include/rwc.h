@@ -284,7 +284,10 @@ rwc_status rwc_solve(rwc_graph_t *g, int32_t k, const double *B, double *X,
  * Johnson-Lindenstrauss sketch: Q_iu = +-1/sqrt(k), the sign the top bit of
  * Philox output o0 for counter (i, u, 0xFFFFFFFF, 0) and key sketch_seed;
  * k = 0 means Q = I (exact, k = n right-hand sides; small graphs only).
- * c: FP64 [n] device, c_u >= 0.  grad_w: FP32 [nnz/2] device, one entry per
+ * c: FP64 [n] device, any signs: the term sum_u c_u (L^+ b_e)_u^2 and
+ * tr(C L^+) are linear in c, so negative entries get their own k sketch
+ * columns with C^1/2 replaced by (max(-c, 0))^1/2 and enter with sign -
+ * (the solve then has 2k + 2 right-hand sides).  grad_w: FP32 [nnz/2] device, one entry per
  * undirected edge in the order of arcs (a, b) with a < b in CSR order (the
  * repeated arcs of a multi-edge each get the same value).
  * Synchronises stream.

@@ -17,7 +17,7 @@ from ._binding import (RWCError, Options, Stats, GraphInfo, lib, lib_path,
                        rwc_batch_roots, rwc_autotune, rwc_batch_get_schedule, rwc_batch_set_schedule, rwc_batch_destroy, rwc_mre, rwc_kendall, rwc_auto_params, Params, rwc_trap_walks, rwc_predict_mre,
                        MODE_AUTO, MODE_GLOBAL, MODE_SHARED, MODE_WALKER, GRAPH_INT64_OFFSETS,
                        GRAPH_SKIP_CONNECTIVITY)
-from .api import Graph, Batch, RWCFunction, fastwalk, fastwalk_to_target
+from .api import Graph, Batch, RWCFunction, fastwalk, fastwalk_auto, fastwalk_to_target
 
 __all__ = [
     "RWCError", "Options", "Stats", "GraphInfo", "lib", "lib_path", "rwc_version",
@@ -28,5 +28,5 @@ __all__ = [
     "rwc_batch_get_schedule", "rwc_batch_set_schedule",
     "rwc_batch_destroy", "rwc_mre", "rwc_kendall", "rwc_auto_params", "Params", "rwc_trap_walks", "rwc_predict_mre", "MODE_AUTO", "MODE_GLOBAL", "MODE_SHARED", "MODE_WALKER",
     "GRAPH_INT64_OFFSETS", "GRAPH_SKIP_CONNECTIVITY", "Graph", "Batch", "RWCFunction",
-    "fastwalk", "fastwalk_to_target",
+    "fastwalk", "fastwalk_auto", "fastwalk_to_target",
 ]

@@ -110,6 +110,29 @@ def fastwalk_to_target(graph: Graph, target_mre: float, first_trees: int = 256,
         T += extra
 
 
+def fastwalk_auto(graph: Graph, eps: float, seed: int = 1, max_trees: int = 1 << 26,
+                  theta_floor: float = 1e-12, stream=None):
+    """Algorithm 3 (FastWalk) with its own parameters: the tree count l of the
+    tree-count lemma and the LapSolve accuracy theta of the performance
+    theorem, both from rwc_auto_params for the given eps.  theta is used as the
+    pivot solve's relative residual, floored at ``theta_floor`` (the FP64
+    residual refinement does not reach further).  The lemma's l is a
+    worst-case bound that grows as t^2 with t = log(...) / log(lambda): on
+    slowly mixing graphs it runs to 1e8 and more trees, so l above
+    ``max_trees`` raises ValueError instead of sampling.  Returns (H, params,
+    solver tolerance used)."""
+    if not 0 < eps:
+        raise ValueError("eps must be positive")
+    p = B.rwc_auto_params(graph.handle, eps, stream=stream)
+    if p.trees > max_trees:
+        raise ValueError(f"the tree-count lemma asks for {p.trees} trees at eps={eps} "
+                         f"(lambda={p.lambda_:.6f}, t={p.t:.1f}); above max_trees={max_trees}")
+    tol = max(float(p.theta), float(theta_floor))
+    sums, _, _, _ = graph.sample(int(p.trees), seed=seed, stream=stream)
+    H = graph.estimate(sums, int(p.trees), tol=tol, stream=stream)
+    return H, p, tol
+
+
 class Batch:
     def __init__(self, graphs):
         """graphs: sequence of objects with row_ptr, col, w (synth.Graph)."""
@@ -224,10 +247,7 @@ def _make_function():
         @staticmethod
         def backward(ctx, gout):
             c = gout.detach().double().contiguous()
-            pos, neg = c.clamp(min=0), (-c).clamp(min=0)
-            grad = ctx.g.grad(pos.contiguous(), ctx.k, ctx.sketch_seed).double()
-            if bool((neg > 0).any()):
-                grad = grad - ctx.g.grad(neg.contiguous(), ctx.k, ctx.sketch_seed).double()
+            grad = ctx.g.grad(c, ctx.k, ctx.sketch_seed)
             return grad.to(device=ctx.w_device, dtype=gout.dtype), None, None, None, None, None, None
 
     return RWCFunction

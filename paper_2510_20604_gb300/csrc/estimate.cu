@@ -87,41 +87,55 @@ __global__ void transpose64(int64_t rows, int64_t cols, const double *in, double
     }
 }
 
-// Gradient right-hand sides, node-major [n][K+2]:
-//   columns i < K: sqrt(c_u) Q_iu (Q Rademacher +-1/sqrt(K) from Philox, or
-//   Q = I when exact), column K: c_u, column K+1: d_u.
-__global__ void grad_rhs(int64_t n, int K, int exact, const double *c, const double *d,
+// Gradient right-hand sides, node-major [n][NP K + 2], NP = 1 or 2 parts:
+//   columns i < K: sqrt(c+_u) Q_iu, and with NP = 2 columns K + i:
+//   sqrt(c-_u) Q_iu (c+ = max(c, 0), c- = max(-c, 0); the same Q for both
+//   parts; Q Rademacher +-1/sqrt(K) from Philox, or Q = I when exact),
+//   column NP K: c_u, column NP K + 1: d_u.  sum_u c_u phi_u^2 is linear in c,
+//   so the two parts' sketches enter the gradient with signs + and -.
+__global__ void grad_rhs(int64_t n, int K, int NP, int exact, const double *c, const double *d,
                          uint32_t k0, uint32_t k1, double *R) {
-    const int64_t cols = (int64_t)K + 2, tot = n * cols;
+    const int64_t KS = (int64_t)NP * K, cols = KS + 2, tot = n * cols;
     const double scale = exact ? 1.0 : 1.0 / sqrt((double)K);
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t u = idx / cols;
-        const int i = (int)(idx - u * cols);
+        const int64_t j = idx - u * cols;
         double val;
-        if (i == K) val = c[u];
-        else if (i == K + 1) val = d[u];
+        if (j == KS) val = c[u];
+        else if (j == KS + 1) val = d[u];
         else {
+            const int part = (int)(j / K), i = (int)(j - (int64_t)part * K);
             double q;
             if (exact) q = (i == u) ? 1.0 : 0.0;
             else {
                 const Ctr4 o = philox4x32_10(Ctr4{(uint32_t)i, (uint32_t)u, 0xFFFFFFFFu, 0u}, k0, k1);
                 q = (o.x >> 31) ? -scale : scale;
             }
-            val = sqrt(c[u]) * q;
+            const double cu = part == 0 ? fmax(c[u], 0.0) : fmax(-c[u], 0.0);
+            val = sqrt(cu) * q;
         }
         R[idx] = val;
     }
 }
 
-// tr(Z C^1/2 Q^T) = sum_u sum_{i<K} X[u][i] R[u][i]
-__global__ void grad_trace(int64_t n, int K, const double *X, const double *R, double *out) {
-    const int64_t cols = (int64_t)K + 2, tot = n * cols;
+// 1 in *flag if some c_u < 0 (the signed split needs the second part).
+__global__ void any_negative(int64_t n, const double *c, int *flag) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * blockDim.x)
+        if (c[u] < 0.0) *flag = 1;
+}
+
+// tr(C L^+) estimate tr(Z C^1/2 Q^T) = sum_u sum_i X[u][i] R[u][i] over the
+// sketch columns, the second part (c-) with sign -.
+__global__ void grad_trace(int64_t n, int K, int NP, const double *X, const double *R, double *out) {
+    const int64_t KS = (int64_t)NP * K, cols = KS + 2, tot = n * cols;
     double s = 0.0;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(idx % cols);
-        if (i < K) s += X[idx] * R[idx];
+        const int64_t j = idx % cols;
+        if (j < K) s += X[idx] * R[idx];
+        else if (j < KS) s -= X[idx] * R[idx];
     }
     s = warp_sum(s);
     if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(out, s);
@@ -155,11 +169,13 @@ __global__ void upper_counts(DevGraph g, int32_t *cnt, int32_t *first) {
     }
 }
 
-// dJ/dw_e for every arc (a, b) with a < b; one warp per row.
+// dJ/dw_e for every arc (a, b) with a < b; one warp per row.  Columns of X:
+// NP K sketch columns (the c- part with sign -), then x = L^+ c, y = L^+ d.
 template <bool OFF64>
-__global__ void grad_edges(DevGraph g, int K, const double *X, const int64_t *off,
+__global__ void grad_edges(DevGraph g, int K, int NP, const double *X, const int64_t *off,
                            const int32_t *first, const double *scal, float *out) {
-    const int64_t cols = (int64_t)K + 2;
+    const int KS = NP * K;
+    const int64_t cols = (int64_t)KS + 2;
     const double trCP = scal[0], dTy = scal[1], csum = scal[2];
     const double vol = g.vol;
     const int lane = threadIdx.x & 31;
@@ -168,17 +184,17 @@ __global__ void grad_edges(DevGraph g, int K, const double *X, const int64_t *of
     for (int64_t a = warp; a < g.n; a += nwarps) {
         const int64_t rb = OFF64 ? g.rp64[a] : g.rp32[a];
         const int64_t re = OFF64 ? g.rp64[a + 1] : g.rp32[a + 1];
-        const double xa = X[a * cols + K], ya = X[a * cols + K + 1];
+        const double xa = X[a * cols + KS], ya = X[a * cols + KS + 1];
         for (int64_t j = rb + first[a]; j < re; ++j) {
             const int64_t b = g.col[j];
             double sq = 0.0;
-            for (int i = lane; i < K; i += 32) {
+            for (int i = lane; i < KS; i += 32) {
                 const double df = X[a * cols + i] - X[b * cols + i];
-                sq += df * df;
+                sq += (i < K) ? df * df : -(df * df);
             }
             sq = warp_sum(sq);
             if (lane == 0) {
-                const double xb = X[b * cols + K], yb = X[b * cols + K + 1];
+                const double xb = X[b * cols + KS], yb = X[b * cols + KS + 1];
                 const double gval = 2.0 * trCP - vol * sq + 2.0 * (xa - xb) * (ya - yb) - 2.0 * (xa + xb) +
                                     csum * ((2.0 * (ya + yb) - (ya - yb) * (ya - yb)) / vol -
                                             2.0 * dTy / (vol * vol));
@@ -266,7 +282,22 @@ extern "C" rwc_status rwc_grad(rwc_graph_t *G, const double *c, int32_t k, uint6
     const int K = exact ? (int)n : k;
     if (exact && n > 16384) return set_error(RWC_ERR_UNSUPPORTED, "exact gradient (k = 0) needs n <= 16384");
     cudaStream_t st = (cudaStream_t)stream;
-    const int64_t cols = (int64_t)K + 2;
+    // signed c: a second set of K sketch columns for the negative part
+    int NP = 1;
+    {
+        int *flag = nullptr;
+        RWC_CUDA_TRY(cudaMallocAsync((void **)&flag, sizeof(int), st));
+        RWC_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
+        ::rwc::count_launches(1); any_negative<<<grid_for(n), TPB, 0, st>>>(n, c, flag);
+        int h = 0;
+        const cudaError_t e1 = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+        const cudaError_t e2 = cudaStreamSynchronize(st);
+        cudaFreeAsync(flag, st);
+        RWC_CUDA_TRY(e1);
+        RWC_CUDA_TRY(e2);
+        NP = h ? 2 : 1;
+    }
+    const int64_t cols = (int64_t)NP * K + 2;
     Buf buf(st);
     const size_t bytes = (size_t)n * cols * 2 * sizeof(double) + (size_t)n * (8 + 4 + 4) + 256;
     RWC_CUDA_TRY(cudaMallocAsync(&buf.p, bytes, st));
@@ -274,13 +305,13 @@ extern "C" rwc_status rwc_grad(rwc_graph_t *G, const double *c, int32_t k, uint6
     int64_t *off = (int64_t *)(X + (size_t)n * cols);
     int32_t *cnt = (int32_t *)(off + n), *first = cnt + n;
     double *scal = (double *)(((uintptr_t)(first + n) + 63) & ~(uintptr_t)63);
-    ::rwc::count_launches(1); grad_rhs<<<grid_for(n * cols), TPB, 0, st>>>(n, K, exact, c, g.d, (uint32_t)seed,
+    ::rwc::count_launches(1); grad_rhs<<<grid_for(n * cols), TPB, 0, st>>>(n, K, NP, exact, c, g.d, (uint32_t)seed,
                                                  (uint32_t)(seed >> 32), R);
     RWC_CUDA_TRY(cudaGetLastError());
     RWC_TRY(solve_nodemajor(G, (int)cols, R, X, tol > 0 ? tol : 1e-8, nullptr, st));
     RWC_CUDA_TRY(cudaMemsetAsync(scal, 0, 4 * sizeof(double), st));
-    ::rwc::count_launches(1); grad_trace<<<grid_for(n * cols), TPB, 0, st>>>(n, K, X, R, scal);
-    ::rwc::count_launches(1); col_dot<<<grid_for(n), TPB, 0, st>>>(n, cols, K + 1, X, g.d, scal + 1);   // d^T y
+    ::rwc::count_launches(1); grad_trace<<<grid_for(n * cols), TPB, 0, st>>>(n, K, NP, X, R, scal);
+    ::rwc::count_launches(1); col_dot<<<grid_for(n), TPB, 0, st>>>(n, cols, cols - 1, X, g.d, scal + 1);   // d^T y
     ::rwc::count_launches(1); dot64<<<grid_for(n), TPB, 0, st>>>(n, c, nullptr, scal + 2);              // sum c
     dispatch_off(g, [&](auto o64) {
         ::rwc::count_launches(1); upper_counts<decltype(o64)::value><<<grid_for(n), TPB, 0, st>>>(g, cnt, first);
@@ -294,7 +325,7 @@ extern "C" rwc_status rwc_grad(rwc_graph_t *G, const double *c, int32_t k, uint6
     for (int64_t a = 0; a < n; ++a) { ho[a] = acc; acc += hc[a]; }
     RWC_CUDA_TRY(cudaMemcpyAsync(off, ho.data(), (size_t)n * 8, cudaMemcpyHostToDevice, st));
     dispatch_off(g, [&](auto o64) {
-        ::rwc::count_launches(1); grad_edges<decltype(o64)::value><<<grid_for(n * 32), TPB, 0, st>>>(g, K, X, off, first, scal, grad_w);
+        ::rwc::count_launches(1); grad_edges<decltype(o64)::value><<<grid_for(n * 32), TPB, 0, st>>>(g, K, NP, X, off, first, scal, grad_w);
     });
     RWC_CUDA_TRY(cudaGetLastError());
     RWC_CUDA_TRY(cudaStreamSynchronize(st));

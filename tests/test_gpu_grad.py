@@ -19,6 +19,16 @@ def _edges(g):
     return a, b, (np.ones(len(a)) if w is None else w.astype(np.float64))
 
 
+def _assert_per_edge(got, ref, rtol, floor_frac=1e-6):
+    """Every edge within rtol of the reference, relative to its own
+    magnitude; only entries smaller than floor_frac of the largest are
+    judged against that floor instead (FP32 output, FP64 arithmetic)."""
+    scale = np.abs(ref).max()
+    den = np.maximum(np.abs(ref), floor_frac * scale)
+    rel = np.abs(got - ref) / den
+    assert rel.max() <= rtol, (rel.max(), int(rel.argmax()))
+
+
 def test_exact_gradient_matches_dense_and_fd():
     g = synth.rgg(200, 12.0, seed=0, sigma=0.5)
     G = rwc.Graph.from_synth(g)
@@ -27,16 +37,39 @@ def test_exact_gradient_matches_dense_and_fd():
     gg = G.grad(ct, k=0, tol=1e-10).double().cpu().numpy()
     a, b, w = _edges(g)
     ref = og.grad_closed(g.n, a, b, w, c)
-    scale = np.abs(ref).max()
-    assert np.max(np.abs(gg - ref)) <= 1e-3 * scale
-    rel = np.abs(gg - ref) / np.maximum(np.abs(ref), 1e-3 * scale)
-    assert np.median(rel) < 1e-4
-    sel = np.random.default_rng(1).choice(len(a), 25, replace=False)
-    for e in sel:
-        wp = w.copy(); wp[e] += 1e-5
-        wm = w.copy(); wm[e] -= 1e-5
-        fd = (og.J(g.n, a, b, wp, c) - og.J(g.n, a, b, wm, c)) / 2e-5
-        assert abs(gg[e] - fd) <= 1e-3 * max(abs(fd), 1e-2 * scale)
+    _assert_per_edge(gg, ref, 1e-3)
+    # central finite differences of the dense exact J on every edge
+    fd = og.grad_fd(g.n, a, b, w, c, h=1e-5)
+    _assert_per_edge(gg, fd, 1e-3)
+
+
+def test_exact_gradient_signed_objective():
+    """c with both signs: the library splits C into its positive and
+    negative parts itself; per edge within 1e-3 of the dense closed form and
+    of central finite differences."""
+    g = synth.rgg(150, 10.0, seed=2, sigma=0.5)
+    G = rwc.Graph.from_synth(g)
+    c = synth.uniform_vector(g.n, 21) - 0.5
+    assert (c < 0).any() and (c > 0).any()
+    gg = G.grad(torch.tensor(c, dtype=torch.float64, device="cuda"), k=0, tol=1e-10).double().cpu().numpy()
+    a, b, w = _edges(g)
+    _assert_per_edge(gg, og.grad_closed(g.n, a, b, w, c), 1e-3)
+    _assert_per_edge(gg, og.grad_fd(g.n, a, b, w, c, h=1e-5), 1e-3)
+
+
+def test_sketch_gradient_signed_objective():
+    """Sketch mode with signed c equals the oracle's sketch of the positive
+    part minus that of the negative part, with the same Philox sketch."""
+    g = synth.rgg(250, 10.0, seed=8, sigma=0.5)
+    G = rwc.Graph.from_synth(g)
+    c = synth.uniform_vector(g.n, 9) - 0.3
+    k, seed = 64, 99
+    gg = G.grad(torch.tensor(c, dtype=torch.float64, device="cuda"), k=k, sketch_seed=seed,
+                tol=1e-10).double().cpu().numpy()
+    a, b, w = _edges(g)
+    Q = ow.rademacher(k, g.n, seed)
+    ref = og.grad_sketch(g.n, a, b, w, np.maximum(c, 0), Q) - og.grad_sketch(g.n, a, b, w, np.maximum(-c, 0), Q)
+    _assert_per_edge(gg, ref, 1e-3)
 
 
 def test_sketch_gradient_matches_oracle_sketch():
@@ -49,10 +82,10 @@ def test_sketch_gradient_matches_oracle_sketch():
     a, b, w = _edges(g)
     Q = ow.rademacher(k, g.n, seed)
     ref = og.grad_sketch(g.n, a, b, w, c, Q)
-    assert np.max(np.abs(gg - ref)) <= 1e-4 * np.abs(ref).max()
+    _assert_per_edge(gg, ref, 1e-3)
     exact = og.grad_closed(g.n, a, b, w, c)
     err = np.linalg.norm(gg - exact) / np.linalg.norm(exact)
-    assert err < 0.5  # JL error at k = 64, reported by the benchmark as a number
+    assert err < 0.5  # JL error at k = 64 (the benchmark line reports it as a number)
 
 
 def test_autograd_function_backward():
@@ -66,6 +99,20 @@ def test_autograd_function_backward():
     assert np.max(np.abs(wt.grad.cpu().numpy() - ref)) <= 1e-3 * np.abs(ref).max()
 
 
+def test_autograd_function_signed_cotangent():
+    """A loss whose cotangent has both signs goes through one library call
+    (the library splits the signs): the backward equals the dense gradient of
+    sum_v c_v H_v with signed c."""
+    g = synth.rgg(60, 8.0, seed=7, sigma=0.3)
+    a, b, w = _edges(g)
+    wt = torch.tensor(w, dtype=torch.float64, requires_grad=True)
+    H = rwc.RWCFunction.apply(wt, g.row_ptr, g.col, 64, 1, 0, 0)
+    c = torch.tensor(synth.uniform_vector(g.n, 3) - 0.5, dtype=torch.float64, device=H.device)
+    (H * c).sum().backward()
+    ref = og.grad_closed(g.n, a, b, w, c.cpu().numpy())
+    _assert_per_edge(wt.grad.cpu().numpy(), ref, 1e-3)
+
+
 def test_exact_gradient_on_parallel_arcs():
     """A weighted graph with doubled and tripled edges: one gradient entry per
     (a < b) arc, parallel copies equal, against the dense closed form."""
@@ -77,6 +124,6 @@ def test_exact_gradient_on_parallel_arcs():
     gg = G.grad(ct, k=0, tol=1e-10).double().cpu().numpy()
     a, b, w = _edges(g)
     ref = og.grad_closed(g.n, a, b, w, c)
-    assert np.max(np.abs(gg - ref)) <= 1e-3 * np.abs(ref).max()
+    _assert_per_edge(gg, ref, 1e-3)
     same = (np.diff(a) == 0) & (np.diff(b) == 0)
     assert same.any() and np.allclose(gg[1:][same], gg[:-1][same], rtol=1e-6, atol=0)

@@ -81,3 +81,44 @@ def test_full_size_diameter(which):
     if which == "grid1024":
         assert p.diameter == 2046
     assert 0.0 < p.mu < 1.0 and p.iterations < 30
+
+
+def _trapped_star():
+    u = [0] * 10 + [1]
+    v = list(range(1, 11)) + [2]
+    return synth.from_edges(11, u, v, np.array([1.0] * 10 + [1e-4], np.float32))
+
+
+def test_walk_bound_clamp_on_device():
+    """The graph where the printed walk-length formula gives about 0.26: the
+    device's t is one step, as the oracle's."""
+    g = _trapped_star()
+    G = rwc.Graph.from_synth(g)
+    p = rwc.rwc_auto_params(G.handle, 0.3)
+    ref = op.auto_params(g, G.root, 0.3)
+    assert G.root == 0 and p.t == 1.0 == ref["t"]
+    assert p.trees == ref["trees"]
+    assert p.lambda_ == pytest.approx(ref["lambda"], rel=1e-6)
+
+
+def test_fastwalk_auto_uses_the_algorithms_parameters():
+    """fastwalk_auto samples l = rwc_auto_params(eps).trees trees and solves
+    to theta (floored at 1e-12): its l and theta are the oracle's, its H is
+    that of fastwalk with the same l and tolerance, and every vertex meets
+    the performance theorem's guarantee pi_u |H~_u - H_u| <= eps against the
+    dense exact centrality."""
+    from oracle import exact as ex
+    g = _trapped_star()
+    G = rwc.Graph.from_synth(g)
+    eps = 0.3
+    H, p, tol = rwc.fastwalk_auto(G, eps, seed=5)
+    ref = op.auto_params(g, G.root, eps)
+    assert p.trees == ref["trees"] and tol == pytest.approx(max(ref["theta"], 1e-12), rel=1e-9)
+    H2, _ = rwc.fastwalk(G, int(p.trees), seed=5, tol=tol)
+    assert np.allclose(H.cpu().numpy(), H2.cpu().numpy(), rtol=1e-11, atol=0)
+    Hx = ex.rwc_pinv(g)
+    d = ow.wdeg(g)
+    pi = d / d.sum()
+    assert np.all(pi * np.abs(H.cpu().numpy() - Hx) <= eps)
+    with pytest.raises(ValueError):
+        rwc.fastwalk_auto(rwc.Graph.from_synth(synth.ba(2000, 3, seed=0)), 0.3)   # l ~ 3e8

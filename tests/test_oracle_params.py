@@ -81,3 +81,37 @@ def test_lambda_of_parallel_arcs_is_that_of_summed_weights():
         lam_m = op.spectral_radius_pv(g, 0)
         lam_s = op.spectral_radius_pv(simple, 0)
         assert lam_m == pytest.approx(lam_s, rel=1e-6)
+
+
+def _trapped_star(w_light=1e-4):
+    """Star with centre 0 and ten unit-weight leaves, plus one light edge
+    between leaves 1 and 2: a walk from any leaf reaches the centre (the
+    pivot) at its first step with probability at least 1 / (1 + w_light)."""
+    import synth
+    u = [0] * 10 + [1]
+    v = list(range(1, 11)) + [2]
+    w = np.array([1.0] * 10 + [w_light], np.float32)
+    return synth.from_edges(11, u, v, w)
+
+
+def test_walk_bound_is_one_step_when_walks_are_trapped_at_once():
+    """The walk-length bound counts steps: when every walk is trapped at its
+    first step but for a fraction below 1/n, one step suffices, although the
+    printed formula's value is below one (here about 0.26).  lambda is pinned
+    by its closed form: P_v keeps only the two light arcs, each of
+    probability w / (1 + w)."""
+    g = _trapped_star()
+    v = 0
+    d = op.degrees(g)
+    m = d.sum() / 2.0
+    lam = op.spectral_radius_pv(g, v)
+    wl = float(np.float32(1e-4))
+    assert lam == pytest.approx(wl / (1.0 + wl), rel=1e-9)
+    assert lam < 1.0 / g.n                      # untrapped after one step: < 1/n
+    dn = float(np.sqrt(np.sum(np.delete(d, v) ** 2)))
+    raw = math.log(m / (g.n * math.sqrt(g.n - 1) * dn)) / math.log(lam)
+    assert raw < 1.0
+    assert op.walk_bound(g.n, m, dn, lam) == 1.0
+    p = op.auto_params(g, v, 0.3)
+    assert p["t"] == 1.0
+    assert p["trees"] == math.ceil(2.0 * math.log(2.0 * g.n) / 0.09)
