@@ -30,14 +30,15 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// out += sum_i a[i] * b[i] (b may be NULL: sum a).
-__global__ void dot64(int64_t n, const double *a, const double *b, double *out) {
+// parts[block] = this block's share of sum_i a[i] * b[i] (b may be NULL:
+// sum a), in a fixed order; sum_parts adds the blocks in order.
+__global__ void dot64(int64_t n, const double *a, const double *b, double *parts) {
     double s = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         s += b ? a[i] * b[i] : a[i];
-    s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(out, s);
+    s = block_sum_fixed(s);
+    if (threadIdx.x == 0) parts[blockIdx.x] = s;
 }
 
 // Algorithm 1, right-hand side: b = sqrt(d_v) e_v - (sqrt(d_v) / vol) d.
@@ -235,15 +236,16 @@ extern "C" rwc_status rwc_estimate(rwc_graph_t *G, const double *sums, int64_t T
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = g.n;
     Buf buf(st);
-    RWC_CUDA_TRY(cudaMallocAsync(&buf.p, (size_t)n * 3 * sizeof(double) + 64, st));
+    const unsigned gs = grid_for(n);
+    RWC_CUDA_TRY(cudaMallocAsync(&buf.p, (size_t)n * 3 * sizeof(double) + (size_t)(gs + 8) * sizeof(double), st));
     double *b = (double *)buf.p, *z = b + n, *y = y_out ? y_out : z + n;
     double *dz = (double *)((char *)buf.p + (size_t)n * 3 * sizeof(double));
-    const unsigned gs = grid_for(n);
+    double *parts = dz + 8;
     ::rwc::count_launches(1); rhs_pivot<<<gs, TPB, 0, st>>>(n, g.d, g.root, g.vol, b);
     RWC_CUDA_TRY(cudaGetLastError());
     RWC_TRY(solve_nodemajor(G, 1, b, z, tol > 0 ? tol : 1e-10, nullptr, st));
-    RWC_CUDA_TRY(cudaMemsetAsync(dz, 0, sizeof(double), st));
-    ::rwc::count_launches(1); dot64<<<gs, TPB, 0, st>>>(n, g.d, z, dz);
+    ::rwc::count_launches(1); dot64<<<gs, TPB, 0, st>>>(n, g.d, z, parts);
+    ::rwc::count_launches(1); sum_parts<<<1, TPB, 0, st>>>(parts, (int)gs, 0, 1, dz);
     ::rwc::count_launches(1); y_from_z<<<gs, TPB, 0, st>>>(n, g.d, z, dz, g.vol, y);
     ::rwc::count_launches(1); recover<<<gs, TPB, 0, st>>>(n, g.d, g.root, g.vol, sums, 1.0 / (double)T, y, H);
     RWC_CUDA_TRY(cudaGetLastError());
@@ -312,7 +314,11 @@ extern "C" rwc_status rwc_grad(rwc_graph_t *G, const double *c, int32_t k, uint6
     RWC_CUDA_TRY(cudaMemsetAsync(scal, 0, 4 * sizeof(double), st));
     ::rwc::count_launches(1); grad_trace<<<grid_for(n * cols), TPB, 0, st>>>(n, K, NP, X, R, scal);
     ::rwc::count_launches(1); col_dot<<<grid_for(n), TPB, 0, st>>>(n, cols, cols - 1, X, g.d, scal + 1);   // d^T y
-    ::rwc::count_launches(1); dot64<<<grid_for(n), TPB, 0, st>>>(n, c, nullptr, scal + 2);              // sum c
+    {   // sum c, in a fixed order (the parts reuse the offsets buffer before it is filled)
+        double *cparts = (double *)off;
+        ::rwc::count_launches(1); dot64<<<grid_for(n), TPB, 0, st>>>(n, c, nullptr, cparts);
+        ::rwc::count_launches(1); sum_parts<<<1, TPB, 0, st>>>(cparts, (int)grid_for(n), 0, 1, scal + 2);
+    }
     dispatch_off(g, [&](auto o64) {
         ::rwc::count_launches(1); upper_counts<decltype(o64)::value><<<grid_for(n), TPB, 0, st>>>(g, cnt, first);
     });

@@ -162,6 +162,38 @@ __device__ __forceinline__ int32_t succ(const DevGraph &g, int32_t u, uint32_t c
 // Library-wide kernel launch counter (graph.cu).
 void count_launches(int64_t k);
 
+// ------------------------------------------------ fixed-order reductions
+// A sum whose order does not depend on scheduling: each thread adds its
+// grid-stride elements in index order, a warp combines its lanes with a fixed
+// shuffle tree, and thread 0 adds the block's warps in warp order.  Blocks
+// store their sums in parts[blockIdx.x] and sum_parts (one block) adds the
+// parts in block order, so a launch of the same size on the same input gives
+// the same bits every time.
+__device__ __forceinline__ double block_sum_fixed(double v) {
+    __shared__ double ws[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();   // an earlier call's reader is done with ws
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) s += ws[w];
+    return s;   // meaningful in thread 0
+}
+
+// out[j] = sum over b < nparts of parts[j * stride + b], in order of b, for
+// j < nvals.  One block: thread t adds parts t, t + blockDim, ... in order,
+// then block_sum_fixed.  (static: every translation unit has its own copy.)
+static __global__ void sum_parts(const double *parts, int nparts, int stride, int nvals, double *out) {
+    for (int j = 0; j < nvals; ++j) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < nparts; b += blockDim.x) s += parts[(int64_t)j * stride + b];
+        s = block_sum_fixed(s);
+        if (threadIdx.x == 0) out[j] = s;
+    }
+}
+
 // SM count of the current device, cached per device index.
 inline int num_sms() {
     static std::atomic<int> cache[64];

@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(TPB) spmm32(DevGraph g, int k, const float *__
 // average degree): Q = L P (FP32) and pq += <P, Q> (FP64).
 template <int VW, bool OFF64, bool W>
 __global__ void __launch_bounds__(TPB) spmv32(DevGraph g, const float *__restrict__ P,
-                                              float *__restrict__ Q, double *pq) {
+                                              float *__restrict__ Q, double *parts) {
     const int sub = threadIdx.x & (VW - 1);
     const int64_t row0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / VW;
     const int64_t nrows = ((int64_t)gridDim.x * blockDim.x) / VW;
@@ -125,15 +125,15 @@ __global__ void __launch_bounds__(TPB) spmv32(DevGraph g, const float *__restric
             acc += (double)pu * (double)q;
         }
     }
-    acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(pq, acc);
+    acc = block_sum_fixed(acc);
+    if (threadIdx.x == 0) parts[blockIdx.x] = acc;
 }
 
 // k == 1 residual R = B - L X (FP64), column sum into colsum[0].
 template <int VW, bool OFF64, bool W>
 __global__ void __launch_bounds__(TPB) resid1(DevGraph g, const double *__restrict__ B,
                                               const double *__restrict__ X, double *__restrict__ R,
-                                              double *colsum) {
+                                              double *parts) {
     const int sub = threadIdx.x & (VW - 1);
     const int64_t row0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / VW;
     const int64_t nrows = ((int64_t)gridDim.x * blockDim.x) / VW;
@@ -154,8 +154,8 @@ __global__ void __launch_bounds__(TPB) resid1(DevGraph g, const double *__restri
             acc += r;
         }
     }
-    acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(colsum, acc);
+    acc = block_sum_fixed(acc);
+    if (threadIdx.x == 0) parts[blockIdx.x] = acc;
 }
 
 // R = B - L X in FP64 (node-major), and the column sums of R.
@@ -263,6 +263,71 @@ __global__ void colsum64(int64_t n, int k, const double *V, double *colsum) {
     sh_flush(sn, k, colsum);
 }
 
+// Single right-hand side versions with fixed-order block parts (the pivot
+// solve of rwc_estimate gives the same bits on every run).
+// V -= colsum / n; parts: sum of V^2.
+__global__ void center1(int64_t n, double *V, const double *colsum, double *parts) {
+    double acc = 0.0;
+    const double m = colsum[0] / (double)n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = V[i] - m;
+        V[i] = v;
+        acc += v * v;
+    }
+    acc = block_sum_fixed(acc);
+    if (threadIdx.x == 0) parts[blockIdx.x] = acc;
+}
+
+// parts: sum of V.
+__global__ void sum1(int64_t n, const double *V, double *parts) {
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        acc += V[i];
+    acc = block_sum_fixed(acc);
+    if (threadIdx.x == 0) parts[blockIdx.x] = acc;
+}
+
+// r = R / |R|, e = 0, z = D^-1 r, p = z; parts: <r, z>.
+__global__ void inner_start1(int64_t n, const double *R, const double *rnrm2, const float *dinv,
+                             float *r, float *e, float *z, float *p, double *parts) {
+    double acc = 0.0;
+    const double nr = sqrt(rnrm2[0]);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float rv = nr > 0 ? (float)(R[i] / nr) : 0.f;
+        const float zv = dinv[i] * rv;
+        r[i] = rv; e[i] = 0.f; z[i] = zv; p[i] = zv;
+        acc += (double)rv * (double)zv;
+    }
+    acc = block_sum_fixed(acc);
+    if (threadIdx.x == 0) parts[blockIdx.x] = acc;
+}
+
+// alpha = rz / pq; e += alpha p; r -= alpha q; z = D^-1 r; parts: <r, z>
+// at [0, stride), <r, r> at [stride, 2 stride).
+__global__ void inner_update1(int64_t n, const double *rz, const double *pq, const float *dinv,
+                              const float *p, const float *q, float *e, float *r, float *z,
+                              double *parts, int stride) {
+    double a1 = 0.0, a2 = 0.0;
+    const double den = pq[0];
+    const float a = (den > 0.0 && rz[0] > 0.0) ? (float)(rz[0] / den) : 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        e[i] += a * p[i];
+        const float rv = r[i] - a * q[i];
+        r[i] = rv;
+        const float zv = dinv[i] * rv;
+        z[i] = zv;
+        a1 += (double)rv * (double)zv;
+        a2 += (double)rv * (double)rv;
+    }
+    a1 = block_sum_fixed(a1);
+    a2 = block_sum_fixed(a2);
+    if (threadIdx.x == 0) { parts[blockIdx.x] = a1; parts[stride + blockIdx.x] = a2; }
+}
+
 // Start of an inner solve: r = R / |R_c| (FP32), e = 0, z = D^-1 r, p = z,
 // rz0[c] = <r, z>.
 __global__ void inner_start(int64_t n, int k, const double *R, const double *rnrm2,
@@ -319,12 +384,45 @@ __global__ void inner_update(int64_t n, int k, const double *rz, const double *p
     }
 }
 
+// Grid-wide sums in a fixed order inside a cooperative launch: every block
+// stores its block_sum_fixed in parts, the grid synchronises, and every block
+// adds all the parts in block order, so all blocks hold the same bits.  The
+// parts are read through L2 (other SMs wrote them).
+__device__ __forceinline__ double bcast0(double v) {
+    __shared__ double b;
+    if (threadIdx.x == 0) b = v;
+    __syncthreads();
+    const double r = b;
+    return r;
+}
+__device__ __forceinline__ double gather_parts(const double *parts) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += __ldcg(parts + i);
+    return bcast0(block_sum_fixed(s));
+}
+__device__ double grid_sum_fixed(cg::grid_group &grid, double v, double *parts) {
+    v = block_sum_fixed(v);
+    if (threadIdx.x == 0) parts[blockIdx.x] = v;
+    grid.sync();
+    return gather_parts(parts);
+}
+__device__ void grid_sum_fixed2(cg::grid_group &grid, double &v1, double &v2, double *p1, double *p2) {
+    const double b1 = block_sum_fixed(v1);
+    const double b2 = block_sum_fixed(v2);
+    if (threadIdx.x == 0) { p1[blockIdx.x] = b1; p2[blockIdx.x] = b2; }
+    grid.sync();
+    v1 = gather_parts(p1);
+    v2 = gather_parts(p2);
+}
+
 // One-launch inner PCG for a single right-hand side (cooperative launch,
-// grid-wide synchronisation between the phases of an iteration).  Scalars of
-// iteration it live at sc[3 it + {0: <p,q>, 1: <r,z>, 2: <r,r>}]; every block
-// reads the same reduced values after a grid sync, so the loop exit (relative
-// residual at most tol, or no halving of <r,r> for `window` iterations, or
-// max_it) is taken by all blocks together.  out[0] = iterations, out[1] = last <r,r>.
+// grid-wide synchronisation between the phases of an iteration).  The
+// iteration's sums <p,q>, <r,z> and <r,r> are grid_sum_fixed results, the
+// same in every block, so the loop exit (relative residual at most tol, or no
+// halving of <r,r> for `window` iterations, or max_it) is taken by all blocks
+// together, and the same input gives the same bits on every run.  sc[1] holds
+// the starting <r,z>; parts: three arrays of gridDim doubles.  out[0] =
+// iterations, out[1] = last <r,r>.
 // Rows with more than HEAVY_DEG arcs are left out of the sub-warp product;
 // each of their HEAVY_CHUNK-arc chunks gets one warp, which stores its partial
 // sum in hsum and adds its share of <p, q> (p_u d_u p_u for a row's first
@@ -333,17 +431,18 @@ __global__ void inner_update(int64_t n, int k, const double *rz, const double *p
 template <int VW, bool OFF64, bool W>
 __global__ void __launch_bounds__(TPB) cg1_coop(DevGraph g, const float *__restrict__ dinv,
                                                 float *r, float *e, float *z, float *p, float *q,
-                                                float *hsum, double *sc, int max_it, double tol2,
-                                                int window, double *out) {
+                                                float *hsum, const double *sc, double *parts,
+                                                int max_it, double tol2, int window, double *out) {
     cg::grid_group grid = cg::this_grid();
     const int sub = threadIdx.x & (VW - 1);
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
     const int64_t row0 = tid / VW, nrows = nthr / VW;
-    double best = INFINITY, rr = sc[2] > 0 ? sc[2] : 1.0;
+    double best = INFINITY, rr = 1.0;
+    double rz = sc[1];
+    double *pA = parts, *pB = parts + gridDim.x, *pC = parts + 2 * (size_t)gridDim.x;
     int since = 0, it = 0;
     for (; it < max_it; ++it) {
-        double *cur = sc + 3 * (size_t)it, *nxt = cur + 3;
         // q = L p and <p, q>
         double acc = 0.0;
         for (int64_t u0 = row0 - (row0 % (32 / VW)); u0 < g.n; u0 += nrows) {
@@ -385,11 +484,8 @@ __global__ void __launch_bounds__(TPB) cg1_coop(DevGraph g, const float *__restr
                 }
             }
         }
-        acc = warp_sum(acc);
-        if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(&cur[0], acc);
-        grid.sync();
+        const double den = grid_sum_fixed(grid, acc, pA);
         // step and the new residual
-        const double den = *(volatile double *)&cur[0], rz = *(volatile double *)&cur[1];
         const float a = (den > 0.0 && rz > 0.0) ? (float)(rz / den) : 0.f;
         double a1 = 0.0, a2 = 0.0;
         for (int64_t i = tid; i < g.n; i += nthr) {
@@ -413,20 +509,15 @@ __global__ void __launch_bounds__(TPB) cg1_coop(DevGraph g, const float *__restr
             a1 += (double)rv * (double)zv;
             a2 += (double)rv * (double)rv;
         }
-        a1 = warp_sum(a1);
-        a2 = warp_sum(a2);
-        if ((threadIdx.x & 31) == 0) {
-            if (a1 != 0.0) atomicAdd(&nxt[1], a1);
-            if (a2 != 0.0) atomicAdd(&nxt[2], a2);
-        }
-        grid.sync();
-        rr = *(volatile double *)&nxt[2];
-        const double rz1 = *(volatile double *)&nxt[1];
+        grid_sum_fixed2(grid, a1, a2, pB, pC);
+        rr = a2;
+        const double rz1 = a1;
         if (!(rr == rr) || rr <= tol2) { ++it; break; }
         if (rr < 0.25 * best) { best = rr; since = 0; }
         else if (++since >= window) { ++it; break; }
         // new direction
         const float bta = rz > 0.0 ? (float)(rz1 / rz) : 0.f;
+        rz = rz1;
         for (int64_t i = tid; i < g.n; i += nthr) p[i] = z[i] + bta * p[i];
         grid.sync();
     }
@@ -505,7 +596,9 @@ rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, doub
     const size_t sc_per_it = 3 * (size_t)k;                 // pq, rz, rr per iteration
     const size_t sc_count = (size_t)(max_inner + 4) * sc_per_it + 8 * (size_t)k;
     const size_t hbytes = (size_t)(g.hc_n + 1) * sizeof(float);
-    const size_t bytes = (size_t)nk * sizeof(double) + 5 * fbytes + sc_count * sizeof(double) + hbytes + 1024;
+    constexpr int PMAX = 4096;                             // block parts of one reduction
+    const size_t bytes = (size_t)nk * sizeof(double) + 5 * fbytes + sc_count * sizeof(double) + hbytes +
+                         3 * PMAX * sizeof(double) + 1024;
     RWC_CUDA_TRY(cudaMallocAsync(&buf.p, bytes, st));
     char *q = (char *)buf.p;
     double *R = (double *)q; q += (size_t)nk * sizeof(double);
@@ -517,11 +610,18 @@ rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, doub
     q = (char *)(((uintptr_t)q + 255) & ~(uintptr_t)255);
     double *outer_sc = (double *)q;       // [0,k) colsum, [k,2k) |R|^2, [2k,3k) |B|^2
     double *it_sc = outer_sc + 8 * (size_t)k;
-    float *hsum = (float *)(it_sc + (sc_count - 8 * (size_t)k));   // [hc_n] heavy-chunk sums
+    double *parts = it_sc + (sc_count - 8 * (size_t)k);   // [3][PMAX] fixed-order block parts
+    float *hsum = (float *)(parts + 3 * (size_t)PMAX);   // [hc_n] heavy-chunk sums
     const size_t shk = (size_t)k * sizeof(double), shk2 = 2 * shk;
     const unsigned gs = grid_for(nk), gw = grid_for(n * 32);
     const int vw = pick_vw(g);
     const unsigned gv = grid_for(n * vw);
+    if (gs > (unsigned)PMAX || gv > (unsigned)PMAX) return set_error(RWC_ERR_UNSUPPORTED, "solver grid above %d blocks", PMAX);
+    // k == 1: fixed-order sums (block parts, then sum_parts in block order)
+    auto finish_sum = [&](unsigned blocks, int nvals, double *out) {
+        ::rwc::count_launches(1);
+        sum_parts<<<1, TPB, 0, st>>>(parts, (int)blocks, PMAX, nvals, out);
+    };
     int dev = 0, coop = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
@@ -539,13 +639,19 @@ rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, doub
             if (k == 1) {
                 dispatch_vw(vw, [&](auto V) {
                     resid1<decltype(V)::value, decltype(o64)::value, decltype(wt)::value>
-                        <<<gv, TPB, 0, st>>>(g, B, X, R, outer_sc);
+                        <<<gv, TPB, 0, st>>>(g, B, X, R, parts);
                 });
             } else {
                 resid64<decltype(o64)::value, decltype(wt)::value><<<gw, TPB, shk, st>>>(g, k, B, X, R, outer_sc);
             }
         });
-        ::rwc::count_launches(1); center64<<<gs, TPB, shk, st>>>(n, k, R, outer_sc, outer_sc + k);
+        if (k == 1) {
+            finish_sum(gv, 1, outer_sc);
+            ::rwc::count_launches(1); center1<<<gs, TPB, 0, st>>>(n, R, outer_sc, parts);
+            finish_sum(gs, 1, outer_sc + 1);
+        } else {
+            ::rwc::count_launches(1); center64<<<gs, TPB, shk, st>>>(n, k, R, outer_sc, outer_sc + k);
+        }
         RWC_CUDA_TRY(cudaGetLastError());
         RWC_CUDA_TRY(cudaMemcpyAsync(h.data(), outer_sc, 2 * shk, cudaMemcpyDeviceToHost, st));
         RWC_CUDA_TRY(cudaStreamSynchronize(st));
@@ -565,7 +671,12 @@ rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, doub
             return set_error(RWC_ERR_NOT_CONVERGED, "Laplacian solve reached %d refinements at relative residual %.3g (tol %.3g)", max_outer, worst, tol);
         // inner FP32 PCG on the normalised residual
         RWC_CUDA_TRY(cudaMemsetAsync(it_sc, 0, sc_count * sizeof(double) - 8 * shk, st));
-        ::rwc::count_launches(1); inner_start<<<gs, TPB, shk, st>>>(n, k, R, outer_sc + k, g.dinv32, r, e, z, p, it_sc + 1 * k);
+        if (k == 1) {
+            ::rwc::count_launches(1); inner_start1<<<gs, TPB, 0, st>>>(n, R, outer_sc + 1, g.dinv32, r, e, z, p, parts);
+            finish_sum(gs, 1, it_sc + 1);
+        } else {
+            ::rwc::count_launches(1); inner_start<<<gs, TPB, shk, st>>>(n, k, R, outer_sc + k, g.dinv32, r, e, z, p, it_sc + 1 * k);
+        }
         if (k == 1 && coop_ok) {
             // one cooperative launch for the whole inner solve
             double *outv = outer_sc + 4;
@@ -579,12 +690,13 @@ rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, doub
                     int per_sm = 0;
                     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TPB, 0);
                     if (per_sm < 1) return;
-                    const unsigned blocks = (unsigned)std::min<int64_t>((int64_t)num_sms() * per_sm, gv);
+                    const unsigned blocks = (unsigned)std::min<int64_t>(std::min<int64_t>((int64_t)num_sms() * per_sm, gv), PMAX);
                     const float *dinv = g.dinv32;
                     float *rr_ = r, *ee = e, *zz = z, *pp = p, *qq = Qv, *hs = hsum;
-                    double *scp = it_sc;
+                    const double *scp = it_sc;
+                    double *pts = parts;
                     DevGraph gg = g;
-                    void *args[] = {&gg, &dinv, &rr_, &ee, &zz, &pp, &qq, &hs, &scp, &mi, &t2, &window, &outv};
+                    void *args[] = {&gg, &dinv, &rr_, &ee, &zz, &pp, &qq, &hs, &scp, &pts, &mi, &t2, &window, &outv};
                     ::rwc::count_launches(1);
                     if (cudaLaunchCooperativeKernel((const void *)kern, blocks, TPB, args, 0, st) == cudaSuccess)
                         launched = true;
@@ -617,13 +729,20 @@ rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, doub
                     if (k == 1) {
                         dispatch_vw(vw, [&](auto V) {
                             spmv32<decltype(V)::value, decltype(o64)::value, decltype(wt)::value>
-                                <<<gv, TPB, 0, st>>>(g, p, Qv, pq);
+                                <<<gv, TPB, 0, st>>>(g, p, Qv, parts);
                         });
                     } else {
                         spmm32<decltype(o64)::value, decltype(wt)::value><<<gw, TPB, shk, st>>>(g, k, p, Qv, pq);
                     }
                 });
-                ::rwc::count_launches(1); inner_update<<<gs, TPB, shk2, st>>>(n, k, rz0, pq, g.dinv32, p, Qv, e, r, z, rz1, rr1);
+                if (k == 1) {
+                    finish_sum(gv, 1, pq);
+                    ::rwc::count_launches(1);
+                    inner_update1<<<gs, TPB, 0, st>>>(n, rz0, pq, g.dinv32, p, Qv, e, r, z, parts, PMAX);
+                    finish_sum(gs, 2, rz1);   // rz1, then rr1 = rz1 + 1
+                } else {
+                    ::rwc::count_launches(1); inner_update<<<gs, TPB, shk2, st>>>(n, k, rz0, pq, g.dinv32, p, Qv, e, r, z, rz1, rr1);
+                }
                 ::rwc::count_launches(1); inner_dir<<<gs, TPB, 0, st>>>(n, k, rz0, rz1, z, p);
             }
             RWC_CUDA_TRY(cudaGetLastError());
@@ -645,8 +764,15 @@ rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, doub
     }
     // final projection of X onto 1-perp
     RWC_CUDA_TRY(cudaMemsetAsync(outer_sc, 0, 2 * shk, st));
-    ::rwc::count_launches(1); colsum64<<<gs, TPB, shk, st>>>(n, k, X, outer_sc);
-    ::rwc::count_launches(1); center64<<<gs, TPB, shk, st>>>(n, k, X, outer_sc, outer_sc + k);
+    if (k == 1) {
+        ::rwc::count_launches(1); sum1<<<gs, TPB, 0, st>>>(n, X, parts);
+        finish_sum(gs, 1, outer_sc);
+        ::rwc::count_launches(1); center1<<<gs, TPB, 0, st>>>(n, X, outer_sc, parts);
+        finish_sum(gs, 1, outer_sc + 1);
+    } else {
+        ::rwc::count_launches(1); colsum64<<<gs, TPB, shk, st>>>(n, k, X, outer_sc);
+        ::rwc::count_launches(1); center64<<<gs, TPB, shk, st>>>(n, k, X, outer_sc, outer_sc + k);
+    }
     RWC_CUDA_TRY(cudaGetLastError());
     if (iters_out) *iters_out = total_iters;
     return RWC_OK;

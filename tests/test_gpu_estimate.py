@@ -134,3 +134,18 @@ def test_fastwalk_to_target_stops_at_the_predicted_count():
     Hx = exact.rwc_pinv(g)
     measured = float(np.mean(np.abs(H.cpu().numpy() - Hx) / Hx))
     assert measured < 0.0125, measured
+
+
+@pytest.mark.parametrize("gname", ["ba", "rmat", "weighted_heavy_rows"])
+def test_pivot_solve_is_bit_reproducible(gname):
+    """The pivot solve's sums run in a fixed order (block parts added in block
+    order, no floating-point atomics), so the same input gives the same y and
+    H bits on every call."""
+    g = {"ba": lambda: synth.ba(3000, 3, seed=1),
+         "rmat": lambda: synth.rmat(14, 16, seed=1),
+         "weighted_heavy_rows": lambda: synth.rmat(13, 64, seed=4, sigma=1.0)}[gname]()
+    G = rwc.Graph.from_synth(g)
+    sums, _, _, _ = G.sample(16, seed=2)
+    outs = [G.estimate(sums, 16, want_y=True) for _ in range(4)]
+    for H, y in outs[1:]:
+        assert torch.equal(H, outs[0][0]) and torch.equal(y, outs[0][1])
