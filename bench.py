@@ -47,6 +47,9 @@ WORKLOADS = {
     "rmat20": [("rmat20", 2000)],
     "ba2000": [("ba2000", 1000)],
     "grid512": [("grid512", 64)],
+    # small cases of the default workload's graph families, for ncu captures
+    "grid256": [("grid256", 2000)],
+    "rmat18-2000": [("rmat18", 2000)],
     "rmat18": [("rmat18", 512)],
     "batch4096": [("batch4096", 256)],
     "rmat24": [("rmat24", 500)],
@@ -87,6 +90,12 @@ def algorithmic_bytes(draws, trees, n, weighted, off64):
 # on (code_hash of the .cu file), else reported as null.
 TRAFFIC_PER_DRAW = {
     # family: (bytes per draw, case captured, source file, code hash)
+    "grid": (277.8, "grid 256x256, 2000 trees, 64 walkers per tree: one w_trees launch "
+                     "(589.8 GB over 2.123e9 draws)", "walker.cu",
+             "3e363bf331eb2929c54dda217a155773493c2a291c4ded1f56bb14982baea0bc"),
+    "rmat": (222.3, "R-MAT scale 18, 2000 trees, 64 walkers per tree: one w_trees launch "
+                     "(171.0 GB over 7.693e8 draws)", "walker.cu",
+             "3e363bf331eb2929c54dda217a155773493c2a291c4ded1f56bb14982baea0bc"),
 }
 
 
@@ -125,6 +134,8 @@ def make_graph(key):
         return synth.grid2d(1024, 1024)
     if key == "grid512":
         return synth.grid2d(512, 512)
+    if key == "grid256":
+        return synth.grid2d(256, 256)
     if key == "rmat20":
         return synth.rmat(20, 16, seed=0)
     if key == "rmat18":
@@ -301,8 +312,9 @@ METRIC = "spanning trees/s and RWC nodes/s at <=1% mean rel err; % of HBM roofli
 
 def batch_measure(rwc, torch, dev, steps, warmup, world=1):
     """4096 small graphs (sizes log-uniform in [50, 20000], ER / BA / RGG),
-    256 trees each, autotuned schedule: one persistent launch (replayed from
-    a CUDA graph) against one launch per graph, same trees, same sums."""
+    256 trees each, autotuned schedule: one CUDA-graph launch (two persistent
+    kernels, one per size class, on forked streams) against one launch per
+    graph, same trees, same sums."""
     import synth
     T = WORKLOADS["batch4096"][0][1]
     t0 = time.perf_counter()
@@ -338,9 +350,10 @@ def batch_measure(rwc, torch, dev, steps, warmup, world=1):
         res[name] = {"ms_per_step": ms, "trees_per_s": world * 4096 * T / (ms / 1000.0),
                      "nodes_per_s": world * B.N / (ms / 1000.0), "draws_per_step": int(draws),
                      "same_sums": bool(torch.equal(ref, sums))}
-    th, split, tile = B.schedule()
+    th, split, tile, warp = B.schedule()
     return {"graphs": 4096, "total_vertices": int(B.N), "trees_per_graph": T,
-            "schedule": {"threads": th, "warp_per_tree_up_to_n": split, "trees_per_item": tile},
+            "schedule": {"large_class_threads": th, "small_class_up_to_n": split,
+                         "small_class": "warp-per-tree" if warp else "block-per-tree", "trees_per_item": tile},
             "persistent_graph": res["persistent_graph"], "per_graph_launch": res["per_graph_launch"],
             "speedup_vs_per_graph_launch": res["per_graph_launch"]["ms_per_step"] / res["persistent_graph"]["ms_per_step"],
             "steps": steps, "warmup": warmup, "generation_s": gen_s, "autotune_s": tune_s}

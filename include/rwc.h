@@ -300,8 +300,8 @@ rwc_status rwc_grad(rwc_graph_t *g, const double *c, int32_t k,
  * Batched sampler: many independent small graphs, all trees of all graphs in
  * one persistent launch (captured in a CUDA graph when use_graph != 0).
  * Graphs with more vertices than the schedule's split run one tree per thread
- * block, the others one tree per warp (several trees per block); see
- * rwc_batch_set_schedule and rwc_autotune.
+ * block, the others one tree per warp (several trees per block) or per small
+ * block; see rwc_batch_set_schedule and rwc_autotune.
  * host_graph_offsets: int64 [G+1] vertex offsets of each graph inside the
  * concatenated CSR; host_row_ptr: int64 [N+1] with global arc offsets;
  * host_col_idx: int32 [nnz] LOCAL vertex ids (0..n_g-1); host_w NULL (unit
@@ -327,15 +327,18 @@ rwc_status rwc_batch_roots(const rwc_batch_t *b, int32_t *host_roots);
  * the device; the choice is cached in cache_path (JSON, may be NULL) under a
  * signature of the batch's sizes.  Synchronises stream. */
 rwc_status rwc_autotune(rwc_batch_t *b, const char *cache_path, rwc_stream_t stream);
-/* The batch's schedule: threads per block (a multiple of 32, <= 1024); split:
- * graphs with at most this many vertices run warp-per-tree (0: every graph
- * block-per-tree); tile: trees per work item.  set returns
- * RWC_ERR_UNSUPPORTED when the schedule needs more than 227 KB of shared
- * memory per block (a tree of n vertices takes 11 n + 64 bytes).
- * host_sched: int32 [3] = {threads, split, tile}.  Schedules do not change
- * the sampled trees. */
+/* The batch's schedule.  threads: block size of the large class (graphs with
+ * more than split vertices, one tree per block; a multiple of 32, <= 1024);
+ * split: the largest n of the small class (0: one class); warp: 1 = the small
+ * class runs one tree per warp (8 trees per 256-thread block), 0 = one tree
+ * per 256-thread block; tile: trees per work item.  The two classes run as two
+ * persistent kernels on forked streams inside one CUDA graph.  set returns
+ * RWC_ERR_UNSUPPORTED when a class needs more than 227 KB of shared memory
+ * per block (a tree of n vertices takes 11 n + 64 bytes).  host_sched: int32
+ * [4] = {threads, split, tile, warp}.  Schedules do not change the trees. */
 rwc_status rwc_batch_get_schedule(const rwc_batch_t *b, int32_t *host_sched);
-rwc_status rwc_batch_set_schedule(rwc_batch_t *b, int32_t threads, int32_t split, int32_t tile);
+rwc_status rwc_batch_set_schedule(rwc_batch_t *b, int32_t threads, int32_t split, int32_t tile,
+                                  int32_t warp);
 rwc_status rwc_batch_destroy(rwc_batch_t *b);
 
 /*

@@ -178,11 +178,12 @@ class Batch:
         B.rwc_autotune(self.handle, cache_path, stream)
 
     def schedule(self):
-        """(threads per block, split: largest n run warp-per-tree, trees per item)."""
+        """(large-class threads per block, split, trees per item, small class
+        warp-per-tree)."""
         return B.rwc_batch_get_schedule(self.handle)
 
-    def set_schedule(self, threads, split, tile):
-        B.rwc_batch_set_schedule(self.handle, threads, split, tile)
+    def set_schedule(self, threads, split, tile, warp=1):
+        B.rwc_batch_set_schedule(self.handle, threads, split, tile, warp)
 
     def close(self):
         if getattr(self, "_ptr", None):

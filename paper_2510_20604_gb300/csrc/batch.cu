@@ -1,12 +1,14 @@
-// Batched sampler: all trees of thousands of small graphs in one persistent
+// Batched sampler: all trees of thousands of small graphs in one CUDA-graph
 // launch.  Work items (graph, tile of trees) are pulled from device counters
-// (no grid-wide barrier).  Items of the larger graphs run block-per-tree; the
-// items of graphs with at most `split` vertices run warp-per-tree (every warp
-// of a block pulls its own items and keeps its tree in its own slice of the
-// block's shared memory), or block-per-tree as well when the schedule says so.
-// The autotuner times candidate schedules (block size, split, tile) on the
-// device; the launch of a call is captured once into a CUDA graph and
-// replayed.  Tree state lives in shared memory (smem_tree.cuh).
+// by persistent kernels (no grid-wide barrier).  The graphs are split by size:
+// those with more than `split` vertices run block-per-tree; the others run
+// warp-per-tree (every warp of a block pulls its own items and keeps its tree
+// in its own slice of the block's shared memory) or block-per-tree with small
+// blocks, as the schedule says.  The two classes run as two persistent
+// kernels on forked streams, so each gets the shared-memory size (and thus
+// the occupancy) its own graphs need; the fork and join are captured into the
+// call's CUDA graph, which is replayed.  The autotuner times candidate
+// schedules on the device.  Tree state lives in shared memory (smem_tree.cuh).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -128,17 +130,21 @@ struct rwc_batch {
     std::vector<int32_t> roots;
     DevGraph base;                     // concatenated CSR (local column ids)
     BGraph *graphs = nullptr;
-    // schedule: block size, the largest n run warp-per-tree (0: none), trees
-    // per work item
-    int threads = 256;
+    // schedule: block size of the large graphs, the largest n of the small
+    // class (0: one class), small class warp-per-tree (1) or block-per-tree
+    // with SMALL_THREADS threads (0), trees per work item
+    int threads = 512;
     int split = 1024;
+    int warp = 1;
     int tile = 4;
+    cudaStream_t side = nullptr;       // the small class's stream (forked from the call's)
+    cudaEvent_t fork = nullptr, join = nullptr;
     int max_n[2] = {0, 0};             // largest n of the block / warp item lists
     BItem *items[2] = {nullptr, nullptr};
     int64_t nitems[2] = {0, 0};
     int64_t items_T = -1;              // T the item lists were built for
     int64_t items_tile = -1, items_split = -1;
-    void *scratch = nullptr;           // [0] err, [8] rounds, [16] draws, [32..40) item counters
+    void *scratch = nullptr;           // [0] err, [8] rounds, [16] draws, [32..48) item counters
     std::vector<void *> allocs;
     // captured launches
     cudaGraph_t graph = nullptr;
@@ -169,12 +175,15 @@ void drop_graph(rwc_batch *b) {
 // Bytes of one warp's shared-memory slice for trees of up to n vertices.
 size_t warp_slice_bytes(int n) { return (smem_tree_bytes(n) + 15) & ~(size_t)15; }
 
-// Dynamic shared memory of the persistent kernel for the current schedule.
-size_t batch_smem(const rwc_batch *b) {
-    size_t s = b->nitems[0] ? smem_tree_bytes(b->max_n[0]) : 0;
-    if (b->nitems[1]) s = std::max(s, (size_t)(b->threads / 32) * warp_slice_bytes(b->max_n[1]));
-    return std::max<size_t>(s, 64);
+constexpr int SMALL_THREADS = 256;   // block size of the small class (8 warps)
+
+// Dynamic shared memory of each class's kernel for the current schedule.
+size_t class_smem(const rwc_batch *b, int c) {
+    if (!b->nitems[c]) return 64;
+    if (c == 1 && b->warp) return (size_t)(SMALL_THREADS / 32) * warp_slice_bytes(b->max_n[1]);
+    return std::max<size_t>(smem_tree_bytes(b->max_n[c]), 64);
 }
+size_t batch_smem(const rwc_batch *b) { return std::max(class_smem(b, 0), class_smem(b, 1)); }
 
 // Work items for T trees per graph: list 0 (block-per-tree) holds graphs with
 // more than `split` vertices, list 1 (warp-per-tree) the others; each list
@@ -210,30 +219,48 @@ rwc_status build_items(rwc_batch *b, int64_t T) {
     return RWC_OK;
 }
 
-// Enqueue the persistent launch of one call.
+// Enqueue one call: the large class on st, the small class on the batch's
+// side stream forked from st and joined back.
 rwc_status enqueue(rwc_batch *b, uint64_t seed, int64_t T, double *sums, cudaStream_t st) {
     int *err = (int *)b->scratch;
     unsigned long long *rounds = (unsigned long long *)((char *)b->scratch + 8);
-    int *counters = (int *)((char *)b->scratch + 32);
-    RWC_CUDA_TRY(cudaMemsetAsync((char *)b->scratch + 32, 0, 8, st));
+    int *counters = (int *)((char *)b->scratch + 32);   // [0..1] large class, [2..3] small class
+    RWC_CUDA_TRY(cudaMemsetAsync((char *)b->scratch + 32, 0, 16, st));
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    const size_t smem = batch_smem(b);
-    if (smem > 227 * 1024) return set_error(RWC_ERR_UNSUPPORTED, "batch schedule needs %zu bytes of shared memory", smem);
+    if (batch_smem(b) > 227 * 1024) return set_error(RWC_ERR_UNSUPPORTED, "batch schedule needs %zu bytes of shared memory", batch_smem(b));
+    const bool fork = b->nitems[0] && b->nitems[1];
+    if (fork) {
+        RWC_CUDA_TRY(cudaEventRecord(b->fork, st));
+        RWC_CUDA_TRY(cudaStreamWaitEvent(b->side, b->fork, 0));
+    }
     rwc_status status = RWC_OK;
-    dispatch(b->off64, b->weighted, [&](auto o64, auto wt) {
-        auto kern = b_persistent<decltype(o64)::value, decltype(wt)::value>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, b->threads, smem);
-        if (per_sm < 1) { status = set_error(RWC_ERR_UNSUPPORTED, "batch block does not fit on an SM"); return; }
-        const int64_t warps = b->threads / 32;
-        const int64_t want = std::max<int64_t>(b->nitems[0], (b->nitems[1] + warps - 1) / warps);
-        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * per_sm));
-        ::rwc::count_launches(1);
-        kern<<<(unsigned)blocks, b->threads, smem, st>>>(
-            b->base, b->graphs, b->items[0], b->nitems[0], b->items[1], b->nitems[1], counters,
-            (int)warp_slice_bytes(b->max_n[1]), b->tile, T, k0, k1, (int64_t)1 << 22, sums, err, rounds);
-    });
+    for (int c = 0; c < 2 && status == RWC_OK; ++c) {
+        if (!b->nitems[c]) continue;
+        const bool warp = c == 1 && b->warp;
+        const int threads = c == 0 ? b->threads : SMALL_THREADS;
+        const size_t smem = class_smem(b, c);
+        cudaStream_t s = (c == 1 && fork) ? b->side : st;
+        dispatch(b->off64, b->weighted, [&](auto o64, auto wt) {
+            auto kern = b_persistent<decltype(o64)::value, decltype(wt)::value>;
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+            if (per_sm < 1) { status = set_error(RWC_ERR_UNSUPPORTED, "batch block does not fit on an SM"); return; }
+            const int64_t per_block = warp ? threads / 32 : 1;
+            const int64_t want = (b->nitems[c] + per_block - 1) / per_block;
+            const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * per_sm));
+            ::rwc::count_launches(1);
+            kern<<<(unsigned)blocks, threads, smem, s>>>(
+                b->base, b->graphs, warp ? nullptr : b->items[c], warp ? 0 : b->nitems[c],
+                warp ? b->items[c] : nullptr, warp ? b->nitems[c] : 0, counters + 2 * c,
+                warp ? (int)warp_slice_bytes(b->max_n[c]) : 0, b->tile, T, k0, k1, (int64_t)1 << 22,
+                sums, err, rounds);
+        });
+    }
+    if (fork) {
+        RWC_CUDA_TRY(cudaEventRecord(b->join, b->side));
+        RWC_CUDA_TRY(cudaStreamWaitEvent(st, b->join, 0));
+    }
     RWC_TRY(status);
     RWC_CUDA_TRY(cudaGetLastError());
     return RWC_OK;
@@ -253,7 +280,7 @@ rwc_status finish(rwc_batch *b, rwc_stats_t *stats, int mode, int64_t T, cudaStr
         stats->marked = b->host[2];
         stats->chunks = 1;
         stats->mode = mode;
-        stats->block_threads = mode == 3 ? 0 : b->threads;
+        stats->block_threads = mode == 3 ? 0 : b->threads;   // the large class's block size
     }
     return RWC_OK;
 }
@@ -348,6 +375,13 @@ extern "C" rwc_status rwc_batch_create(int32_t G, const int64_t *voff, const int
     if ((e = cudaMemcpy(b->graphs, hg.data(), G * sizeof(BGraph), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
     if ((e = balloc(b, &b->scratch, 128)) != cudaSuccess) return fail(e);
     if ((e = cudaMallocHost((void **)&b->host, 64)) != cudaSuccess) return fail(e);
+    if ((e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming)) != cudaSuccess) {
+        if (b->fork) cudaEventDestroy(b->fork);
+        if (b->side) cudaStreamDestroy(b->side);
+        return fail(e);
+    }
     *out = b;
     return RWC_OK;
 }
@@ -436,22 +470,30 @@ extern "C" rwc_status rwc_batch_get_schedule(const rwc_batch_t *b, int32_t *host
     host_sched[0] = b->threads;
     host_sched[1] = b->split;
     host_sched[2] = b->tile;
+    host_sched[3] = b->warp;
     return RWC_OK;
 }
 
-extern "C" rwc_status rwc_batch_set_schedule(rwc_batch_t *b, int32_t threads, int32_t split, int32_t tile) {
+extern "C" rwc_status rwc_batch_set_schedule(rwc_batch_t *b, int32_t threads, int32_t split, int32_t tile,
+                                             int32_t warp) {
     clear_error();
-    if (!b || threads < 32 || threads > 1024 || threads % 32 || split < 0 || split > 20000 || tile < 1)
+    if (!b || threads < 32 || threads > 1024 || threads % 32 || split < 0 || split > 20000 || tile < 1 ||
+        (warp != 0 && warp != 1))
         return set_error(RWC_ERR_INVALID, "schedule needs threads in [32, 1024] (a multiple of 32), "
-                                          "0 <= split <= 20000 and tile >= 1");
+                                          "0 <= split <= 20000, tile >= 1 and warp 0 or 1");
     int wmax = 0, bmax = 0;
-    for (const BGraph &g : b->hgraphs) (g.n <= split ? wmax : bmax) = std::max(g.n <= split ? wmax : bmax, g.n);
-    const size_t need = std::max(bmax ? smem_tree_bytes(bmax) : 0, wmax ? (size_t)(threads / 32) * warp_slice_bytes(wmax) : 0);
+    for (const BGraph &g : b->hgraphs) {
+        if (g.n <= split) wmax = std::max(wmax, g.n);
+        else bmax = std::max(bmax, g.n);
+    }
+    const size_t small = wmax ? (warp ? (size_t)(SMALL_THREADS / 32) * warp_slice_bytes(wmax) : smem_tree_bytes(wmax)) : 0;
+    const size_t need = std::max(bmax ? smem_tree_bytes(bmax) : 0, small);
     if (need > 227 * 1024)
         return set_error(RWC_ERR_UNSUPPORTED, "schedule needs %zu bytes of shared memory per block", need);
     b->threads = threads;
     b->split = split;
     b->tile = tile;
+    b->warp = warp;
     b->items_T = -1;
     drop_graph(b);
     return RWC_OK;
@@ -472,18 +514,18 @@ extern "C" rwc_status rwc_autotune(rwc_batch_t *b, const char *cache_path, rwc_s
             buf[len] = 0;
             const char *p = strstr(buf, sig);
             const char *colon = p ? strchr(p, ':') : nullptr;
-            int th, sp, tl;
-            if (colon && sscanf(colon + 1, " [%d, %d, %d]", &th, &sp, &tl) == 3 &&
-                rwc_batch_set_schedule(b, th, sp, tl) == RWC_OK)
+            int th, sp, tl, wp;
+            if (colon && sscanf(colon + 1, " [%d, %d, %d, %d]", &th, &sp, &tl, &wp) == 4 &&
+                rwc_batch_set_schedule(b, th, sp, tl, wp) == RWC_OK)
                 return RWC_OK;
             clear_error();
         }
     }
     double *sums = nullptr;
     RWC_CUDA_TRY(cudaMallocAsync((void **)&sums, b->N * sizeof(double), st));
-    // block size x the largest n run warp-per-tree (0: every tree block-per-tree)
-    // x trees per work item, each timed on 16 trees per graph
-    const int cand_threads[] = {128, 256, 512};
+    // large-class block size x the split x small class warp- or
+    // block-per-tree x trees per work item, each timed on 16 trees per graph
+    const int cand_threads[] = {256, 512};
     const int cand_split[] = {0, 512, 1024, 2048};
     const int cand_tile[] = {1, 4, 16};
     const int64_t Tp = 16;
@@ -491,12 +533,13 @@ extern "C" rwc_status rwc_autotune(rwc_batch_t *b, const char *cache_path, rwc_s
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int bth = b->threads, bsp = b->split, btl = b->tile;
+    int bth = b->threads, bsp = b->split, btl = b->tile, bwp = b->warp;
     rwc_status status = RWC_OK;
     for (int sp : cand_split)
+        for (int wp = 0; wp < (sp ? 2 : 1); ++wp)
         for (int th : cand_threads)
             for (int tl : cand_tile) {
-                b->threads = th; b->split = sp; b->tile = tl;
+                b->threads = th; b->split = sp; b->tile = tl; b->warp = wp;
                 b->items_T = -1;
                 if ((status = build_items(b, Tp)) != RWC_OK) goto done;
                 if (!schedule_fits(b)) continue;
@@ -509,7 +552,7 @@ extern "C" rwc_status rwc_autotune(rwc_batch_t *b, const char *cache_path, rwc_s
                 cudaEventSynchronize(e1);
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best) { best = ms; bth = th; bsp = sp; btl = tl; }
+                if (ms < best) { best = ms; bth = th; bsp = sp; btl = tl; bwp = wp; }
             }
 done:
     cudaEventDestroy(e0);
@@ -517,13 +560,13 @@ done:
     cudaFreeAsync(sums, st);
     RWC_CUDA_TRY(cudaStreamSynchronize(st));
     RWC_TRY(status);
-    b->threads = bth; b->split = bsp; b->tile = btl;
+    b->threads = bth; b->split = bsp; b->tile = btl; b->warp = bwp;
     b->items_T = -1;
     drop_graph(b);
     if (cache_path) {
         FILE *f = fopen(cache_path, "w");
         if (f) {
-            fprintf(f, "{\"%s\": [%d, %d, %d]}\n", sig, bth, bsp, btl);
+            fprintf(f, "{\"%s\": [%d, %d, %d, %d]}\n", sig, bth, bsp, btl, bwp);
             fclose(f);
         }
     }
@@ -533,8 +576,12 @@ done:
 extern "C" rwc_status rwc_batch_destroy(rwc_batch_t *b) {
     if (!b) return RWC_OK;
     drop_graph(b);
+    if (b->side) cudaStreamSynchronize(b->side);
     for (void *p : b->allocs) cudaFree(p);
     if (b->host) cudaFreeHost(b->host);
+    if (b->join) cudaEventDestroy(b->join);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->side) cudaStreamDestroy(b->side);
     delete b;
     return RWC_OK;
 }
