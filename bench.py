@@ -89,24 +89,35 @@ def algorithmic_bytes(draws, trees, n, weighted, off64):
 # draws of its own launches.  Valid only for the kernel source it was measured
 # on (code_hash of the .cu file), else reported as null.
 TRAFFIC_PER_DRAW = {
-    # family: (bytes per draw, case captured, source file, code hash)
-    "grid": (277.8, "grid 256x256, 2000 trees, 64 walkers per tree: one w_trees launch "
-                     "(589.8 GB over 2.123e9 draws)", "walker.cu",
-             "3e363bf331eb2929c54dda217a155773493c2a291c4ded1f56bb14982baea0bc"),
-    "rmat": (222.3, "R-MAT scale 18, 2000 trees, 64 walkers per tree: one w_trees launch "
+    # family: (bytes per draw, case captured, source file, code hash of the kernel region)
+    "grid": (277.4, "grid 256x256, 2000 trees, 64 walkers per tree: one w_trees launch "
+                     "(588.9 GB over 2.123e9 draws)", "walker.cu",
+             "ec78c283b954dd69a2f710758762f74305e75d37e20288e73414d43a0a711341"),
+    "rmat": (222.2, "R-MAT scale 18, 2000 trees, 64 walkers per tree: one w_trees launch "
                      "(171.0 GB over 7.693e8 draws)", "walker.cu",
-             "3e363bf331eb2929c54dda217a155773493c2a291c4ded1f56bb14982baea0bc"),
+             "ec78c283b954dd69a2f710758762f74305e75d37e20288e73414d43a0a711341"),
 }
 
 
-def code_hash(path):
+def code_hash(path, begin=None, end=None):
     """SHA-256 of a source file's code: every line except blank lines and
     lines that hold only a // comment (so that rewording a comment keeps a
-    measurement, while any change to the code voids it)."""
+    measurement, while any change to the code voids it).  With begin/end,
+    only the lines from the first line containing `begin` up to (not
+    including) the first later line containing `end`: the measured kernel."""
     import hashlib
     lines = [ln.rstrip() for ln in open(path, encoding="utf-8")]
+    if begin is not None:
+        i = next(k for k, ln in enumerate(lines) if begin in ln)
+        j = next((k for k in range(i + 1, len(lines)) if end in lines[k]), len(lines))
+        lines = lines[i:j]
     code = [ln for ln in lines if ln.strip() and not ln.strip().startswith("//")]
     return hashlib.sha256("\n".join(code).encode()).hexdigest()
+
+
+# the walker kernel's source region in walker.cu (what a traffic capture measured)
+W_TREES_REGION = ("walker.cu", "__global__ void __maxnreg__(RWC_WALKER_MAXNREG) w_trees(",
+                  "// visits_u = k_u + 1 over the chunk's trees")
 
 
 def family(key):
@@ -122,8 +133,8 @@ def traffic_per_draw(key):
     nbytes, _case, src, sha = ent
     path = os.path.join(ROOT, "paper_2510_20604_gb300", "csrc", src)
     try:
-        cur = code_hash(path)
-    except OSError:
+        cur = code_hash(path, W_TREES_REGION[1], W_TREES_REGION[2])
+    except (OSError, StopIteration):
         return None
     return nbytes if cur == sha else None
 
@@ -350,10 +361,11 @@ def batch_measure(rwc, torch, dev, steps, warmup, world=1):
         res[name] = {"ms_per_step": ms, "trees_per_s": world * 4096 * T / (ms / 1000.0),
                      "nodes_per_s": world * B.N / (ms / 1000.0), "draws_per_step": int(draws),
                      "same_sums": bool(torch.equal(ref, sums))}
-    th, split, tile, warp = B.schedule()
+    th, split, tile, warp, conc = B.schedule()
     return {"graphs": 4096, "total_vertices": int(B.N), "trees_per_graph": T,
             "schedule": {"large_class_threads": th, "small_class_up_to_n": split,
-                         "small_class": "warp-per-tree" if warp else "block-per-tree", "trees_per_item": tile},
+                         "small_class": "warp-per-tree" if warp else "block-per-tree", "trees_per_item": tile,
+                         "classes": "concurrent" if conc else "sequential"},
             "persistent_graph": res["persistent_graph"], "per_graph_launch": res["per_graph_launch"],
             "speedup_vs_per_graph_launch": res["per_graph_launch"]["ms_per_step"] / res["persistent_graph"]["ms_per_step"],
             "steps": steps, "warmup": warmup, "generation_s": gen_s, "autotune_s": tune_s}
@@ -476,10 +488,10 @@ def run_eps_sweep(args, rwc, torch, dev, rank):
     gt_s = time.perf_counter() - t0
     rows = []
     for eps in EPS_SWEEP:
-        rwc.fastwalk_to_target(G, eps, seed=1)      # warm-up of the same call
+        rwc.fastwalk_to_target(G, eps, first_trees=8, seed=1)      # warm-up of the same call
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        H, T, mre_pred = rwc.fastwalk_to_target(G, eps, seed=1)
+        H, T, mre_pred = rwc.fastwalk_to_target(G, eps, first_trees=8, seed=1)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         mre = float(rwc.rwc_mre(Hgt, H).item())

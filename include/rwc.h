@@ -97,7 +97,12 @@ typedef struct {
                                  on), 2 = wait (keep the path until the vertex
                                  changes owner), 3 = yield and take a fresh start
                                  at once while fresh starts remain (the wait of 1
-                                 once only requeued starts are left) */
+                                 once only requeued starts are left), 4 = park:
+                                 the later walk keeps its path, hung at the
+                                 contested vertex, and its thread takes other
+                                 work; the earlier walk takes the later path's
+                                 suffix over (no path is released; 64 walkers
+                                 per tree, 48 B of state per tree-vertex) */
     int64_t max_wait_ns;      /* WALKER mode: a wait inside the sampler fails with
                                  RWC_ERR_NOT_CONVERGED once its thread block (one
                                  tree) has stored no vertex word for this many
@@ -331,14 +336,16 @@ rwc_status rwc_autotune(rwc_batch_t *b, const char *cache_path, rwc_stream_t str
  * more than split vertices, one tree per block; a multiple of 32, <= 1024);
  * split: the largest n of the small class (0: one class); warp: 1 = the small
  * class runs one tree per warp (8 trees per 256-thread block), 0 = one tree
- * per 256-thread block; tile: trees per work item.  The two classes run as two
- * persistent kernels on forked streams inside one CUDA graph.  set returns
+ * per 256-thread block; tile: trees per work item; concurrent: 1 = the two
+ * classes' persistent kernels run on forked streams at the same time, 0 = one
+ * after the other (both inside the call's one CUDA graph).  set returns
  * RWC_ERR_UNSUPPORTED when a class needs more than 227 KB of shared memory
  * per block (a tree of n vertices takes 11 n + 64 bytes).  host_sched: int32
- * [4] = {threads, split, tile, warp}.  Schedules do not change the trees. */
+ * [5] = {threads, split, tile, warp, concurrent}.  Schedules do not change the
+ * trees. */
 rwc_status rwc_batch_get_schedule(const rwc_batch_t *b, int32_t *host_sched);
 rwc_status rwc_batch_set_schedule(rwc_batch_t *b, int32_t threads, int32_t split, int32_t tile,
-                                  int32_t warp);
+                                  int32_t warp, int32_t concurrent);
 rwc_status rwc_batch_destroy(rwc_batch_t *b);
 
 /*

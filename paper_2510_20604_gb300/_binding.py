@@ -102,7 +102,7 @@ def lib():
         "rwc_batch_roots": ([_vp, _vp], _i32),
         "rwc_autotune": ([_vp, ctypes.c_char_p, _vp], _i32),
         "rwc_batch_get_schedule": ([_vp, _vp], _i32),
-        "rwc_batch_set_schedule": ([_vp, _i32, _i32, _i32, _i32], _i32),
+        "rwc_batch_set_schedule": ([_vp, _i32, _i32, _i32, _i32, _i32], _i32),
         "rwc_batch_destroy": ([_vp], _i32),
         "rwc_mre": ([_i64, _vp, _vp, _vp, _vp], _i32),
         "rwc_auto_params": ([_vp, _d, _i32, _d, ctypes.POINTER(Params), _vp], _i32),
@@ -278,14 +278,14 @@ def rwc_autotune(b, cache_path=None, stream=None):
 
 def rwc_batch_get_schedule(b) -> tuple:
     """(large-class threads per block, split: largest n of the small class,
-    trees per item, small class warp-per-tree)."""
-    out = np.zeros(4, np.int32)
+    trees per item, small class warp-per-tree, classes concurrent)."""
+    out = np.zeros(5, np.int32)
     _check(lib().rwc_batch_get_schedule(b, out.ctypes.data))
     return tuple(int(x) for x in out)
 
 
-def rwc_batch_set_schedule(b, threads, split, tile, warp=1):
-    _check(lib().rwc_batch_set_schedule(b, int(threads), int(split), int(tile), int(warp)))
+def rwc_batch_set_schedule(b, threads, split, tile, warp=1, concurrent=1):
+    _check(lib().rwc_batch_set_schedule(b, int(threads), int(split), int(tile), int(warp), int(concurrent)))
 
 
 def rwc_batch_destroy(b):

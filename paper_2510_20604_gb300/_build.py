@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librwc.so")
-SOURCES = ["graph.cu", "sampler.cu", "walker.cu", "solver.cu", "estimate.cu", "batch.cu", "evaluate.cu", "params.cu", "trapwalk.cu"]
+SOURCES = ["graph.cu", "sampler.cu", "walker.cu", "solver.cu", "estimate.cu", "batch.cu", "evaluate.cu", "params.cu", "trapwalk.cu", "park.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

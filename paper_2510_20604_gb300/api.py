@@ -179,11 +179,11 @@ class Batch:
 
     def schedule(self):
         """(large-class threads per block, split, trees per item, small class
-        warp-per-tree)."""
+        warp-per-tree, classes concurrent)."""
         return B.rwc_batch_get_schedule(self.handle)
 
-    def set_schedule(self, threads, split, tile, warp=1):
-        B.rwc_batch_set_schedule(self.handle, threads, split, tile, warp)
+    def set_schedule(self, threads, split, tile, warp=1, concurrent=1):
+        B.rwc_batch_set_schedule(self.handle, threads, split, tile, warp, concurrent)
 
     def close(self):
         if getattr(self, "_ptr", None):

@@ -137,6 +137,7 @@ struct rwc_batch {
     int split = 1024;
     int warp = 1;
     int tile = 4;
+    int conc = 1;                      // 1: the classes run concurrently (forked streams)
     cudaStream_t side = nullptr;       // the small class's stream (forked from the call's)
     cudaEvent_t fork = nullptr, join = nullptr;
     int max_n[2] = {0, 0};             // largest n of the block / warp item lists
@@ -228,7 +229,7 @@ rwc_status enqueue(rwc_batch *b, uint64_t seed, int64_t T, double *sums, cudaStr
     RWC_CUDA_TRY(cudaMemsetAsync((char *)b->scratch + 32, 0, 16, st));
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     if (batch_smem(b) > 227 * 1024) return set_error(RWC_ERR_UNSUPPORTED, "batch schedule needs %zu bytes of shared memory", batch_smem(b));
-    const bool fork = b->nitems[0] && b->nitems[1];
+    const bool fork = b->conc && b->nitems[0] && b->nitems[1];
     if (fork) {
         RWC_CUDA_TRY(cudaEventRecord(b->fork, st));
         RWC_CUDA_TRY(cudaStreamWaitEvent(b->side, b->fork, 0));
@@ -471,16 +472,17 @@ extern "C" rwc_status rwc_batch_get_schedule(const rwc_batch_t *b, int32_t *host
     host_sched[1] = b->split;
     host_sched[2] = b->tile;
     host_sched[3] = b->warp;
+    host_sched[4] = b->conc;
     return RWC_OK;
 }
 
 extern "C" rwc_status rwc_batch_set_schedule(rwc_batch_t *b, int32_t threads, int32_t split, int32_t tile,
-                                             int32_t warp) {
+                                             int32_t warp, int32_t concurrent) {
     clear_error();
     if (!b || threads < 32 || threads > 1024 || threads % 32 || split < 0 || split > 20000 || tile < 1 ||
-        (warp != 0 && warp != 1))
+        (warp != 0 && warp != 1) || (concurrent != 0 && concurrent != 1))
         return set_error(RWC_ERR_INVALID, "schedule needs threads in [32, 1024] (a multiple of 32), "
-                                          "0 <= split <= 20000, tile >= 1 and warp 0 or 1");
+                                          "0 <= split <= 20000, tile >= 1, warp and concurrent 0 or 1");
     int wmax = 0, bmax = 0;
     for (const BGraph &g : b->hgraphs) {
         if (g.n <= split) wmax = std::max(wmax, g.n);
@@ -494,6 +496,7 @@ extern "C" rwc_status rwc_batch_set_schedule(rwc_batch_t *b, int32_t threads, in
     b->split = split;
     b->tile = tile;
     b->warp = warp;
+    b->conc = concurrent;
     b->items_T = -1;
     drop_graph(b);
     return RWC_OK;
@@ -514,59 +517,72 @@ extern "C" rwc_status rwc_autotune(rwc_batch_t *b, const char *cache_path, rwc_s
             buf[len] = 0;
             const char *p = strstr(buf, sig);
             const char *colon = p ? strchr(p, ':') : nullptr;
-            int th, sp, tl, wp;
-            if (colon && sscanf(colon + 1, " [%d, %d, %d, %d]", &th, &sp, &tl, &wp) == 4 &&
-                rwc_batch_set_schedule(b, th, sp, tl, wp) == RWC_OK)
+            int th, sp, tl, wp, cc;
+            if (colon && sscanf(colon + 1, " [%d, %d, %d, %d, %d]", &th, &sp, &tl, &wp, &cc) == 5 &&
+                rwc_batch_set_schedule(b, th, sp, tl, wp, cc) == RWC_OK)
                 return RWC_OK;
             clear_error();
         }
     }
     double *sums = nullptr;
     RWC_CUDA_TRY(cudaMallocAsync((void **)&sums, b->N * sizeof(double), st));
-    // large-class block size x the split x small class warp- or
-    // block-per-tree x trees per work item, each timed on 16 trees per graph
-    const int cand_threads[] = {256, 512};
-    const int cand_split[] = {0, 512, 1024, 2048};
-    const int cand_tile[] = {1, 4, 16};
+    // coordinate search from the current schedule, each candidate timed on
+    // 16 trees per graph: the split with the small class warp- or
+    // block-per-tree, then the large class's block size, then trees per item,
+    // then concurrent or sequential classes
     const int64_t Tp = 16;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    struct Sched { int th, sp, tl, wp, cc; };
+    Sched best_s{b->threads, b->split, b->tile, b->warp, b->conc};
     float best = 1e30f;
-    int bth = b->threads, bsp = b->split, btl = b->tile, bwp = b->warp;
     rwc_status status = RWC_OK;
-    for (int sp : cand_split)
-        for (int wp = 0; wp < (sp ? 2 : 1); ++wp)
-        for (int th : cand_threads)
-            for (int tl : cand_tile) {
-                b->threads = th; b->split = sp; b->tile = tl; b->warp = wp;
-                b->items_T = -1;
-                if ((status = build_items(b, Tp)) != RWC_OK) goto done;
-                if (!schedule_fits(b)) continue;
-                cudaMemsetAsync(b->scratch, 0, 32, st);
-                if (enqueue(b, 12345, Tp, sums, st) != RWC_OK) { clear_error(); continue; }
-                cudaEventRecord(e0, st);
-                cudaMemsetAsync(b->scratch, 0, 32, st);
-                if (enqueue(b, 12346, Tp, sums, st) != RWC_OK) { clear_error(); continue; }
-                cudaEventRecord(e1, st);
-                cudaEventSynchronize(e1);
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best) { best = ms; bth = th; bsp = sp; btl = tl; bwp = wp; }
-            }
+    auto time_one = [&](const Sched &c) -> float {
+        b->threads = c.th; b->split = c.sp; b->tile = c.tl; b->warp = c.wp; b->conc = c.cc;
+        b->items_T = -1;
+        if ((status = build_items(b, Tp)) != RWC_OK) return -1.f;
+        if (!schedule_fits(b)) return 1e30f;
+        cudaMemsetAsync(b->scratch, 0, 32, st);
+        if (enqueue(b, 12345, Tp, sums, st) != RWC_OK) { clear_error(); return 1e30f; }
+        cudaEventRecord(e0, st);
+        cudaMemsetAsync(b->scratch, 0, 32, st);
+        if (enqueue(b, 12346, Tp, sums, st) != RWC_OK) { clear_error(); return 1e30f; }
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    auto consider = [&](Sched c) -> bool {
+        const float ms = time_one(c);
+        if (ms < 0.f) return false;
+        if (ms < best) { best = ms; best_s = c; }
+        return true;
+    };
+    {
+        const int splits[][2] = {{0, 0}, {512, 1}, {1024, 1}, {2048, 1}, {1024, 0}, {2048, 0}, {4096, 0}};
+        for (auto &sw : splits) { Sched c = best_s; c.sp = sw[0]; c.wp = sw[1]; if (!consider(c)) goto done; }
+        const Sched base1 = best_s;
+        for (int th : {256, 512, 1024}) { Sched c = base1; c.th = th; if (!consider(c)) goto done; }
+        const Sched base2 = best_s;
+        for (int tl : {1, 4, 16}) { Sched c = base2; c.tl = tl; if (!consider(c)) goto done; }
+        const Sched base3 = best_s;
+        for (int cc : {0, 1}) { Sched c = base3; c.cc = cc; if (!consider(c)) goto done; }
+    }
 done:
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFreeAsync(sums, st);
     RWC_CUDA_TRY(cudaStreamSynchronize(st));
     RWC_TRY(status);
-    b->threads = bth; b->split = bsp; b->tile = btl; b->warp = bwp;
+    b->threads = best_s.th; b->split = best_s.sp; b->tile = best_s.tl; b->warp = best_s.wp; b->conc = best_s.cc;
     b->items_T = -1;
     drop_graph(b);
     if (cache_path) {
         FILE *f = fopen(cache_path, "w");
         if (f) {
-            fprintf(f, "{\"%s\": [%d, %d, %d, %d]}\n", sig, bth, bsp, btl, bwp);
+            fprintf(f, "{\"%s\": [%d, %d, %d, %d, %d]}\n", sig, best_s.th, best_s.sp, best_s.tl, best_s.wp, best_s.cc);
             fclose(f);
         }
     }

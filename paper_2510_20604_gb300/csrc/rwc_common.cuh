@@ -84,10 +84,16 @@ namespace rwc {
 
 cudaError_t graph_alloc(rwc_graph *G, void **p, size_t bytes);
 
-// Walker sampler (walker.cu).
+// Walker sampler (walker.cu) and its parked-path variant (park.cu, policy 4).
 rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, double *sums,
                          int32_t *parents, int32_t *visits, const rwc_options_t &o,
                          rwc_stats_t *st, cudaStream_t stream);
+rwc_status sample_park(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, double *sums,
+                       int32_t *parents, int32_t *visits, const rwc_options_t &o,
+                       rwc_stats_t *st, cudaStream_t stream);
+// The walkers' start order (a fixed permutation of the non-root vertices, on
+// the device, made on first use and kept with the graph).
+rwc_status walker_order(rwc_graph *G, const int32_t **out);
 
 // Host-side CSR checks (graph.cu): see rwc_graph_create for the rules.
 rwc_status validate_csr(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *col,

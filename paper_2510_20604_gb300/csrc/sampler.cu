@@ -589,7 +589,7 @@ extern "C" rwc_status rwc_sample_trees(rwc_graph_t *G, uint64_t seed, int64_t tr
     o.use_jumps = -1;
     if (opt) o = *opt;
     if (stats) memset(stats, 0, sizeof(*stats));
-    if (o.walker_policy < 0 || o.walker_policy > 3)
+    if (o.walker_policy < 0 || o.walker_policy > 4)
         return set_error(RWC_ERR_INVALID, "unknown walker policy %d", o.walker_policy);
     if (T == 0) return RWC_OK;
     const DevGraph &g = G->g;

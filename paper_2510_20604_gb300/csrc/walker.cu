@@ -531,7 +531,7 @@ void dispatch(const DevGraph &g, F f) {
 
 // Start order shared by every tree of a graph: a fixed pseudo-random
 // permutation of the non-root vertices (the result does not depend on it).
-static rwc_status walker_order(rwc_graph *G, const int32_t **out) {
+rwc_status walker_order(rwc_graph *G, const int32_t **out) {
     if (G->walk_order) { *out = G->walk_order; return RWC_OK; }
     const int64_t n = G->g.n;
     std::vector<int32_t> ord;
@@ -554,6 +554,7 @@ static rwc_status walker_order(rwc_graph *G, const int32_t **out) {
 rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, double *sums,
                          int32_t *parents, int32_t *visits, const rwc_options_t &o,
                          rwc_stats_t *st, cudaStream_t stream) {
+    if (o.walker_policy == 4) return sample_park(G, seed, tree0, T, sums, parents, visits, o, st, stream);
     const DevGraph &g = G->g;
     const int64_t n = g.n;
     if (n >= ((int64_t)1 << 31) - 2) return set_error(RWC_ERR_UNSUPPORTED, "n too large for walker mode");

@@ -48,7 +48,7 @@ def test_code_hash_ignores_comment_lines_only(tmp_path):
 def test_traffic_is_reported_only_for_the_measured_code(tmp_path, monkeypatch):
     b = _bench()
     src = "walker.cu"
-    cur = b.code_hash(os.path.join(ROOT, "paper_2510_20604_gb300", "csrc", src))
+    cur = b.code_hash(os.path.join(ROOT, "paper_2510_20604_gb300", "csrc", src), *b.W_TREES_REGION[1:])
     monkeypatch.setitem(b.TRAFFIC_PER_DRAW, "grid", (250.0, "grid 256x256", src, cur))
     monkeypatch.setitem(b.TRAFFIC_PER_DRAW, "rmat", (99.0, "R-MAT 18", src, "0" * 64))
     assert b.traffic_per_draw("grid1024") == 250.0
@@ -56,6 +56,17 @@ def test_traffic_is_reported_only_for_the_measured_code(tmp_path, monkeypatch):
     assert b.traffic_per_draw("ba2000") is None          # never measured
     for fam, (nbytes, case, s, sha) in b.TRAFFIC_PER_DRAW.items():
         assert nbytes > 0 and case and s.endswith(".cu") and len(sha) == 64
+
+
+def test_code_hash_of_a_region(tmp_path):
+    b = _bench()
+    p = tmp_path / "k.cu"
+    p.write_text("int a() { return 0; }\n// BEGIN k\nint k() {\n  return 1;\n}\n// END\nint z() { return 2; }\n")
+    h0 = b.code_hash(str(p), "BEGIN k", "END")
+    p.write_text("int a() { return 5; }\n// BEGIN k\nint k() {\n  return 1;\n}\n// END\nint z() { return 7; }\n")
+    assert b.code_hash(str(p), "BEGIN k", "END") == h0      # code outside the region changed
+    p.write_text("int a() { return 5; }\n// BEGIN k\nint k() {\n  return 2;\n}\n// END\n")
+    assert b.code_hash(str(p), "BEGIN k", "END") != h0
 
 
 def test_algorithmic_bytes():

@@ -36,8 +36,8 @@ def test_batch_matches_oracle_and_modes_agree():
     assert st.trees == T * len(gs)
 
 
-@pytest.mark.parametrize("sched", [(512, 0, 4, 1), (512, 1024, 4, 1), (256, 1024, 2, 0), (256, 2500, 1, 1),
-                                   (128, 600, 16, 1)])
+@pytest.mark.parametrize("sched", [(512, 0, 4, 1, 1), (512, 1024, 4, 1, 1), (256, 1024, 2, 0, 1),
+                                   (256, 2500, 1, 1, 0), (128, 600, 16, 1, 0)])
 def test_batch_schedules_match_oracle(sched):
     """One class block-per-tree; small graphs warp-per-tree; small graphs
     block-per-tree in small blocks; almost every graph warp-per-tree; a
@@ -63,18 +63,19 @@ def test_batch_schedule_rejects_oversized_slices():
     gs = _graphs(G=6, seed=3, nmax=20000)
     B = rwc.Batch(gs)
     with pytest.raises(rwc.RWCError) as e:
-        B.set_schedule(512, 20000, 1, 1)    # 8 warps x 11 n bytes of shared memory
+        B.set_schedule(512, 20000, 1, 1, 1)    # 8 warps x 11 n bytes of shared memory
     assert e.value.status in (1, 6)
     with pytest.raises(rwc.RWCError):
-        B.set_schedule(100, 0, 1, 0)        # not a multiple of 32
+        B.set_schedule(100, 0, 1, 0, 1)        # not a multiple of 32
 
 
 def test_batch_autotune_and_large_graphs():
     gs = _graphs(G=10, seed=9, nmax=20000)
     B = rwc.Batch(gs)
     B.autotune(None)
-    th, split, tile, warp = B.schedule()
-    assert th % 32 == 0 and tile >= 1 and split in (0, 512, 1024, 2048) and warp in (0, 1)
+    th, split, tile, warp, conc = B.schedule()
+    assert th % 32 == 0 and tile >= 1 and split in (0, 512, 1024, 2048, 4096) and warp in (0, 1)
+    assert conc in (0, 1)
     T = 5
     s, _ = B.sample(T, seed=1)
     sums = s.cpu().numpy()
