@@ -92,6 +92,7 @@ struct PState {
     const int32_t *order;  // [n-1] start order
     int *err;
     unsigned long long *ctr;   // [3] next tree, [4] draws (unused here)
+    unsigned long long *diag;  // [9] DIAG: lane ticks per state, [8] warp ticks
 };
 
 __global__ void p_init(int64_t n, int32_t root, uint4 *word, int *pstat, int64_t B) {
@@ -109,9 +110,10 @@ __global__ void p_init(int64_t n, int32_t root, uint4 *word, int *pstat, int64_t
 
 enum : int { S_IDLE = 0, S_WALK, S_POP, S_SET, S_ADOPT, S_HAND, S_WAITK, S_WAKE, S_DONE };
 
-template <bool OFF64, bool WT>
+template <bool OFF64, bool WT, bool DIAG>
 __global__ void __launch_bounds__(64, 14) w_park(DevGraph g, PState s, int64_t B, uint32_t tree0,
                                              uint32_t k0, uint32_t k1, int64_t max_wait_ns) {
+    unsigned long long it_state[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // DIAG: lane ticks per state
     const int n = (int)g.n;
     const int nstart = n - 1;
     const int me = threadIdx.x;
@@ -242,7 +244,9 @@ __global__ void __launch_bounds__(64, 14) w_park(DevGraph g, PState s, int64_t B
                 atomicOr(&sh_err, PERR_WAIT);
             if (__all_sync(0xffffffffu, state == S_DONE || state == S_WAITK || state == S_IDLE))
                 __nanosleep(100);
+            if (DIAG && (threadIdx.x & 31) == 0) ++it_state[S_DONE];   // warp ticks
             if (state == S_DONE) continue;
+            if (DIAG) ++it_state[state];
             do {
             if (state == S_IDLE) {
                 // 1) a resumable path, 2) a flagged vertex to scan, 3) a fresh
@@ -522,6 +526,9 @@ __global__ void __launch_bounds__(64, 14) w_park(DevGraph g, PState s, int64_t B
         if (me == 0 && sh_err) atomicOr(s.err, sh_err);
         if (sh_err) break;
     }
+    if (DIAG && s.diag)
+        for (int i = 0; i < 9; ++i)
+            if (it_state[i]) atomicAdd(&s.diag[i], it_state[i]);
 }
 
 // visits_u = k_u + 1 over the chunk's trees into sums; optional per-tree output.
@@ -602,6 +609,7 @@ rwc_status sample_park(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, do
     ps.order = order;
     ps.err = (int *)tail;
     ps.ctr = (unsigned long long *)(tail + 8);
+    ps.diag = (unsigned long long *)(tail + 64);
     unsigned long long *draws = (unsigned long long *)(tail + 40);
     const bool prof = o.profile != 0;
     cudaEvent_t ev[4] = {};
@@ -615,7 +623,7 @@ rwc_status sample_park(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, do
     int64_t *h = G->host_scalars;
     for (int64_t c0 = 0; c0 < T; c0 += B) {
         const int64_t Bc = std::min(B, T - c0);
-        RWC_CUDA_TRY(cudaMemsetAsync(tail, 0, 128, stream));
+        RWC_CUDA_TRY(cudaMemsetAsync(tail, 0, 160, stream));
         RWC_CUDA_TRY(cudaMemsetAsync(ps.retry, 0, (size_t)Bc * (n - 1) * 4, stream));
         RWC_CUDA_TRY(cudaMemsetAsync(ps.resume, 0, (size_t)Bc * (n - 1) * 8, stream));
         RWC_CUDA_TRY(cudaMemsetAsync(ps.wake, 0, (size_t)Bc * n * 8, stream));
@@ -625,7 +633,8 @@ rwc_status sample_park(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, do
         if (prof) cudaEventRecord(ev[1], stream);
         rwc_status status = RWC_OK;
         dispatch(g, [&](auto off64, auto wt) {
-            auto kern = w_park<decltype(off64)::value, decltype(wt)::value>;
+            auto kern = (o.profile >= 2) ? w_park<decltype(off64)::value, decltype(wt)::value, true>
+                                         : w_park<decltype(off64)::value, decltype(wt)::value, false>;
             const size_t smem = park_smem(Wc);
             int per_sm = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Wc, smem);
@@ -643,13 +652,17 @@ rwc_status sample_park(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, do
                                              visits ? visits + c0 * n : nullptr, draws);
         if (prof) cudaEventRecord(ev[3], stream);
         RWC_CUDA_TRY(cudaGetLastError());
-        RWC_CUDA_TRY(cudaMemcpyAsync(h, tail, 128, cudaMemcpyDeviceToHost, stream));
+        RWC_CUDA_TRY(cudaMemcpyAsync(h, tail, 160, cudaMemcpyDeviceToHost, stream));
         RWC_CUDA_TRY(cudaStreamSynchronize(stream));
         const int e = (int)(h[0] & 0xffffffff);
         if (e & PERR_LOOP)
             return set_error(RWC_ERR_CUDA, "walker internal check %d failed", (int)(h[0] >> 32));
         if (e & PERR_WAIT) return set_error(RWC_ERR_NOT_CONVERGED, "a walker wait exceeded its bound");
         if (st) {
+            // diag: [0..6] lane ticks in idle, walk, pop, settle, take-over,
+            // hand-over, wait; [7] warp ticks
+            for (int i = 0; i < 7; ++i) st->diag[i] += h[8 + i];
+            st->diag[7] += h[8 + 8];
             st->chunks += 1;
             st->draws += h[5];
             st->marked += h[5];
