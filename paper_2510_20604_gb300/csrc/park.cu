@@ -18,11 +18,14 @@
 // A path is named by the index of its start vertex in the start order; the
 // earliest live path is never parked, so the tree always progresses.
 //
-// Per (tree, vertex): a 16-byte word {successor, pop count, owner path,
-// flags}; flag 1 = some parked path hangs at this vertex.  Whoever settles or
-// frees a flagged vertex queues it; an idle walker then scans the vertex's
-// neighbours for parked heads pointing at it and makes those paths
-// resumable.  Per (tree, path): status and the vertex it hangs at.
+// Per (tree, vertex): a 16-byte word {successor, pop count, owner path, 0},
+// written by its owner with plain stores (claims are a CAS), and a flag: 1 =
+// some parked path hangs at this vertex.  A walk that hangs sets the flag and
+// then checks the vertex's owner again; an owner that settles or frees a
+// vertex stores the word and then takes the flag (fences between, so one of
+// the two sees the other) and queues a flagged vertex; an idle walker scans
+// that vertex's neighbours for parked heads pointing at it and makes those
+// paths resumable.  Per (tree, path): status and the vertex it hangs at.
 // Waits are bounded by a lack of progress; on exhaustion the block records
 // an error and stops.
 #include <algorithm>
@@ -38,7 +41,6 @@ typedef unsigned __int128 u128;
 
 constexpr uint32_t O_FREE = 0xFFFFFFFFu, O_SET = 0xFFFFFFFEu;
 constexpr uint32_t P_NONE = 0xFFFFFFFFu;
-constexpr uint32_t F_ATT = 1u;
 
 // path status (pstat); an active path stores PS_ACTIVE + its walker's index
 constexpr int PS_DEAD = 0, PS_PARKING = 1, PS_PARKED = 2, PS_RESUMABLE = 3, PS_ADOPTING = 4,
@@ -65,6 +67,10 @@ __device__ __forceinline__ uint4 ld4(const uint4 *a) {
                  : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(a) : "memory");
     return r;
 }
+__device__ __forceinline__ void st4(uint4 *a, uint4 v) {
+    asm volatile("st.relaxed.cta.global.v4.u32 [%0], {%1,%2,%3,%4};"
+                 ::"l"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
+}
 __device__ __forceinline__ uint4 cas4(uint4 *a, uint4 cmp, uint4 val) {
     return upk(atomicCAS_block(reinterpret_cast<u128 *>(a), pk(cmp), pk(val)));
 }
@@ -89,6 +95,7 @@ struct PState {
     int *retry;            // [B][n-1] requeued start indices + 1 (ring)
     int *resume;           // [B][2(n-1)] resumable paths + 1 (ring; stale entries are skipped)
     int *wake;             // [B][2n] flagged vertices + 1 (ring)
+    int *flag;             // [B][n] 1: some parked path hangs at this vertex
     const int32_t *order;  // [n-1] start order
     int *err;
     unsigned long long *ctr;   // [3] next tree, [4] draws (unused here)
@@ -108,11 +115,19 @@ __global__ void p_init(int64_t n, int32_t root, uint4 *word, int *pstat, int64_t
         pstat[i] = PS_DEAD;
 }
 
-enum : int { S_IDLE = 0, S_WALK, S_POP, S_SET, S_ADOPT, S_HAND, S_WAITK, S_WAKE, S_DONE };
+// Walker states.  Every tick a walker does at most: one 16-byte vertex-word
+// load, one int load (a path status, a hang point or a neighbour id) and the
+// row bounds of a vertex it may draw for, all issued together; then at most
+// one 16-byte CAS and one int CAS, issued together.  So the lanes of a warp
+// pay about two dependent memory round trips per tick whatever mix of states
+// they are in (a state machine that ran each state's accesses in its own
+// branch paid them once per state present in the warp).
+enum : int { S_IDLE = 0, S_WALK, S_POP, S_SET, S_ADOPT, S_HAND, S_WAITK, S_WAKE, S_DONE,
+             S_POPX, S_HANG, S_QCHK, S_ADPREP };
 
 template <bool OFF64, bool WT, bool DIAG>
 __global__ void __launch_bounds__(64, 14) w_park(DevGraph g, PState s, int64_t B, uint32_t tree0,
-                                             uint32_t k0, uint32_t k1, int64_t max_wait_ns) {
+                                                 uint32_t k0, uint32_t k1, int64_t max_wait_ns) {
     unsigned long long it_state[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // DIAG: lane ticks per state
     const int n = (int)g.n;
     const int nstart = n - 1;
@@ -149,14 +164,20 @@ __global__ void __launch_bounds__(64, 14) w_park(DevGraph g, PState s, int64_t B
         int *retry = s.retry + (int64_t)t * nstart;
         int *resume = s.resume + (int64_t)t * 2 * nstart;
         int *wake = s.wake + (int64_t)t * 2 * n;
+        int *flag = s.flag + (int64_t)t * n;
         const uint32_t tree = tree0 + (uint32_t)t;
 
         int state = S_IDLE;
         const uint64_t tree_t0 = gclock();
         int path = -1, start = -1, head = -1, hp = -1, cur = -1, popx = -1, aq = -1, qv = -1;
-        int kw = -1, kp = -1, end = -1, walked = 0;
+        int kp = -1, end = -1, walked = 0;
+        int hg_p = -1, hg_a = -1, hg_next = S_IDLE;   // S_HANG: path, vertex, state after
+        int wv = -1, wj = 0;                            // S_WAKE: neighbour in hand, next arc
+        int64_t rbx = 0;                                // row of popx (S_POPX), of qv (S_WAKE)
+        uint32_t degx = 0;
         uint32_t kx = 0;
         uint32_t polls = 0;
+        int pend_v = -1, pend_f = 0;   // the flag taken from vertex pend_v last tick
 
         auto vread = [](const int *a) { return *(const volatile int *)a; };
         auto progress = [&]() { *(volatile unsigned *)&sh_prog = (unsigned)clock(); };
@@ -198,44 +219,42 @@ __global__ void __launch_bounds__(64, 14) w_park(DevGraph g, PState s, int64_t B
             return v - 1;
         };
         auto is_path = [&](uint32_t o) { return o < (uint32_t)nstart; };
+        auto bad = [&](int v) {
+            if ((unsigned)v >= (unsigned)n) { fail(3); return true; }
+            return false;
+        };
         auto die = [&]() {
             sti(pstat + path, PS_DEAD);
             atomicSub(&sh_live, 1);
             path = -1; head = -1; state = S_IDLE; polls = 0;
         };
-        // hang path p's head at vertex a (owned by an earlier path, or by the
-        // walk that took p's suffix over): status first, then the flag on a;
-        // false when a changed under us (p is then made resumable)
-        auto hang = [&](int p, int a) {
-            if ((unsigned)a >= (unsigned)n) { fail(2); return false; }
+        // start hanging path p's head at vertex a: status, then the flag on
+        // a, then (S_HANG, next tick) a's owner is looked at again: if a is
+        // still an earlier path's, p is parked, else p is made resumable;
+        // then the state becomes `next`
+        auto begin_hang = [&](int p, int a, int next) {
             sti(patt + p, a);
             sti(pstat + p, PS_PARKING);
             __threadfence_block();
-            for (int tries = 0; tries < 64; ++tries) {
-                const uint4 w = ld4(W + a);
-                if (!is_path(w.z) || (int)w.z >= p) break;   // a left an earlier path
-                uint4 nw = w;
-                nw.w |= F_ATT;
-                // always an atomic on a (also when the flag is already set), so
-                // that it is ordered with the owner's atomic that frees or
-                // settles a and then queues a for waking
-                if (same(cas4(W + a, w, nw), w)) {
-                    atomicCAS(pstat + p, PS_PARKING, PS_PARKED);
-                    return true;
-                }
-            }
-            // a is free, settled or later-owned: p must look again itself
-            if (atomicCAS(pstat + p, PS_PARKING, PS_RESUMABLE) == PS_PARKING)
-                push(resume, &rs_t, &rs_h, 2 * nstart, p);
-            return false;
+            atomicOr(flag + a, 1);
+            __threadfence_block();
+            hg_p = p; hg_a = a; hg_next = next;
+            state = S_HANG;
+        };
+        // an owner's settle or free of vertex v: word first, then the flag
+        // (its value is looked at next tick)
+        auto release_flag = [&](int v) {
+            __threadfence_block();
+            pend_f = atomicExch(flag + v, 0);
+            pend_v = v;
+        };
+        auto draw = [&](int v, uint32_t c, int64_t rb, uint32_t deg) -> int {
+            const Ctr4 o = philox4x32_10(Ctr4{c, (uint32_t)v, tree, 0u}, k0, k1);
+            const uint32_t j = __umulhi(o.x, deg);
+            if (WT) { const WArc arc = g.warc[rb + j]; return (o.y < arc.thr) ? arc.col : arc.alias_col; }
+            return __ldg(g.col + rb + j);
         };
 
-        // a vertex index about to be used: out of range ends the tree with
-        // an internal error instead of an access outside the buffers
-        auto bad = [&](int v) {
-            if ((unsigned)v >= (unsigned)n) { fail(3); return true; }
-            return false;
-        };
         for (uint32_t tick = 0;; ++tick) {
             if (__any_sync(0xffffffffu, vread(&sh_err) != 0)) break;
             if (__all_sync(0xffffffffu, state == S_DONE)) break;
@@ -245,282 +264,357 @@ __global__ void __launch_bounds__(64, 14) w_park(DevGraph g, PState s, int64_t B
             if (__all_sync(0xffffffffu, state == S_DONE || state == S_WAITK || state == S_IDLE))
                 __nanosleep(100);
             if (DIAG && (threadIdx.x & 31) == 0) ++it_state[S_DONE];   // warp ticks
+            if (pend_v >= 0) {
+                if (pend_f) push(wake, &wk_t, &wk_h, 2 * n, pend_v);
+                pend_v = -1;
+            }
             if (state == S_DONE) continue;
-            if (DIAG) ++it_state[state];
-            do {
+            if (DIAG) ++it_state[state <= S_WAKE ? state : state == S_POPX ? S_POP : S_WALK];
+
+            // ---------------- phase A: work that needs no vertex word
             if (state == S_IDLE) {
                 // 1) a resumable path, 2) a flagged vertex to scan, 3) a fresh
                 // start, 4) a requeued start
                 const int q = pop(resume, &rs_h, &rs_t, 2 * nstart);
                 if (q >= 0) {
-                    if (atomicCAS(pstat + q, PS_RESUMABLE, PS_ACTIVE + me) != PS_RESUMABLE) break;  // stale
-                    path = q; start = s.order[q]; head = -2; hp = ldi(patt + q);
-                    k_v[me] = -1; mb_ok[me] = 0;
-                    state = S_WALK; polls = 0; progress();
-                    break;
+                    if (atomicCAS(pstat + q, PS_RESUMABLE, PS_ACTIVE + me) == PS_RESUMABLE) {
+                        path = q; start = s.order[q]; head = -2; hp = ldi(patt + q);
+                        k_v[me] = -1; mb_ok[me] = 0;
+                        state = S_WALK; polls = 0; progress();
+                    }
+                } else {
+                    const int v = pop(wake, &wk_h, &wk_t, 2 * n);
+                    if (v >= 0) {
+                        qv = v;
+                        if (!bad(v)) {
+                            row_bounds<OFF64>(g, v, rbx, degx);
+                            wj = 0; wv = -1; state = S_WAKE; polls = 0;
+                        }
+                    } else {
+                        int idx = -1;
+                        if (vread(&sh_next) < nstart) {
+                            const int i = atomicAdd(&sh_next, 1);
+                            if (i < nstart) idx = i;
+                        }
+                        if (idx < 0) idx = pop(retry, &rq_h, &rq_t, nstart);
+                        if (idx >= 0) {
+                            path = idx; start = s.order[idx]; head = -1; hp = -1;
+                            k_v[me] = -1; mb_ok[me] = 0;
+                            state = S_WALK; polls = 0;
+                        } else if (vread(&sh_live) == 0 && vread(&sh_next) >= nstart &&
+                                   vread(&rq_h) >= vread(&rq_t) && vread(&rs_h) >= vread(&rs_t) &&
+                                   vread(&wk_h) >= vread(&wk_t)) {
+                            state = S_DONE;
+                        } else {
+                            waited_out();
+                        }
+                    }
                 }
-                const int v = pop(wake, &wk_h, &wk_t, 2 * n);
-                if (v >= 0) { qv = v; cur = 0; state = S_WAKE; polls = 0; break; }
-                int idx = -1;
-                if (vread(&sh_next) < nstart) {
-                    const int i = atomicAdd(&sh_next, 1);
-                    if (i < nstart) idx = i;
-                }
-                if (idx < 0) idx = pop(retry, &rq_h, &rq_t, nstart);
-                if (idx >= 0) {
-                    path = idx; start = s.order[idx]; head = -1; hp = -1;
-                    k_v[me] = -1; mb_ok[me] = 0;
-                    state = S_WALK; polls = 0;
-                    break;
-                }
-                if (vread(&sh_live) == 0 && vread(&sh_next) >= nstart && vread(&rq_h) >= vread(&rq_t) &&
-                    vread(&rs_h) >= vread(&rs_t) && vread(&wk_h) >= vread(&wk_t))
-                    state = S_DONE;
-                else if (waited_out())
-                    break;
-                break;
-            }
-            if (state == S_WAKE) {
-                // vertex qv was settled or freed while paths hung at it: one
-                // neighbour per tick, a parked head there pointing at qv wakes
-                if (bad(qv)) break;
-                int64_t rb; uint32_t deg;
-                row_bounds<OFF64>(g, qv, rb, deg);
-                if (cur >= (int)deg) { state = S_IDLE; break; }
-                const int h = WT ? g.warc[rb + cur].col : __ldg(g.col + rb + cur);
-                ++cur;
-                if (bad(h)) break;
-                __threadfence_block();
-                const uint4 w = ld4(W + h);
-                if (is_path(w.z) && (int)w.x == qv) {
-                    const int p = (int)w.z;
-                    const int st = ldi(pstat + p);
-                    if ((st == PS_PARKED || st == PS_PARKING) && ldi(patt + p) == qv &&
-                        atomicCAS(pstat + p, st, PS_RESUMABLE) == st)
-                        push(resume, &rs_t, &rs_h, 2 * nstart, p);
-                }
-                break;
+                continue;   // the new state's first access comes next tick
             }
             if (state == S_WAITK) {
-                // asked the active path aq for vertex cur: wait for the suffix
                 if (vread(&mb_ok[me])) {
                     mb_ok[me] = 0;
                     *(volatile int *)&wait_for[me] = -1;
                     head = mb_h[me]; hp = mb_p[me];
                     state = S_WALK; polls = 0; progress();
+                    continue;
+                }
+                if (vread(&wait_for[me]) == HAND_BUSY) { waited_out(); continue; }   // handover under way
+            }
+
+            // ---------------- phase B: the tick's loads, issued together
+            int la = -1;                 // vertex word
+            const int *aux = nullptr;    // int (status, hang point, neighbour id)
+            int rowv = -1;               // row bounds of a vertex that may be drawn for
+            switch (state) {
+                case S_WALK: la = head == -1 ? start : hp; rowv = la; break;
+                case S_POP: la = cur; if (cur == head) rowv = popx; break;
+                case S_POPX: la = popx; break;
+                case S_SET: case S_ADOPT: case S_HAND: la = cur; break;
+                case S_WAITK: la = cur; aux = pstat + aq; break;
+                case S_WAKE:
+                    la = wv;
+                    if (wj < (int)degx) aux = WT ? &g.warc[rbx + wj].col : g.col + rbx + wj;
                     break;
-                }
-                if (vread(&wait_for[me]) == HAND_BUSY) { if (waited_out()) break; break; }   // handover under way
-                if (bad(cur)) break;
-                const uint4 w = ld4(W + cur);
-                const int st = ldi(pstat + aq);
-                if ((int)w.z != aq || st == PS_PARKED || st == PS_RESUMABLE) {
-                    // the situation changed: withdraw, unless aq has just
-                    // committed to hand over (then wait for the mailbox)
-                    if (atomicCAS(&wait_for[me], aq, -1) == aq) { state = S_WALK; polls = 0; }
-                    break;
-                }
-                if (st >= PS_ACTIVE) {
-                    const int vw = st - PS_ACTIVE;
-                    const int other = vread(&k_w[vw]);
-                    if (vread(&k_v[vw]) != aq || other < 0 || other >= (int)blockDim.x ||
-                        vread(&req_p[other]) > path) {
-                        // (re)post: the victim reads this walker's own
-                        // request fields, which stay fixed while it waits
-                        *(volatile int *)&k_w[vw] = me;
-                        __threadfence_block();
-                        *(volatile int *)&k_v[vw] = aq;
-                    }
-                }
-                if (waited_out()) break;
-                break;
+                case S_HANG: la = hg_a; break;
+                case S_QCHK: la = hp; aux = pstat + aq; break;
+                case S_ADPREP: la = hp; aux = patt + aq; break;
+                default: break;
             }
-            if (state == S_HAND) {
-                // hand the suffix cur .. head over to path kp (walker kw)
-                if (bad(cur)) break;
-                const uint4 w = ld4(W + cur);
-                if ((int)w.z != path || ++walked > n) { fail(4); break; }
-                uint4 nw = w;
-                nw.z = (uint32_t)kp;
-                if (!same(cas4(W + cur, w, nw), w)) break;   // a flag arrived: again
-                progress();
-                if ((int)w.x == hp) {
-                    // cur was the head: post the mailbox, park the prefix
-                    mb_h[kw] = cur; mb_p[kw] = hp;
-                    __threadfence_block();
-                    *(volatile int *)&mb_ok[kw] = 1;
-                    if (end == start) {
-                        // the whole path moved, start included: its start is
-                        // looked at again later (a later pop could free it)
-                        push(retry, &rq_t, &rq_h, nstart, path);
-                        die();
-                        break;
-                    }
-                    hang(path, end);
-                    path = -1; head = -1; state = S_IDLE; polls = 0;
-                    break;
-                }
-                cur = (int)w.x;
-                break;
-            }
-            if (state == S_ADOPT) {
-                // take the parked path aq's suffix cur .. (the vertex before its
-                // hang point `end`) over as this path's
-                if (bad(cur)) break;
-                const uint4 w = ld4(W + cur);
-                if ((int)w.z != aq || ++walked > n) { fail(5); break; }
-                uint4 nw = w;
-                nw.z = (uint32_t)path;
-                if (!same(cas4(W + cur, w, nw), w)) break;
-                progress();
-                if ((int)w.x == end) {
-                    head = cur; hp = end;
-                    // aq keeps its prefix, now hanging at the first adopted vertex
-                    if (s.order[aq] == qv) {
-                        sti(pstat + aq, PS_DEAD);
-                        atomicSub(&sh_live, 1);
-                        push(retry, &rq_t, &rq_h, nstart, aq);
-                    } else {
-                        hang(aq, qv);
-                    }
-                    state = S_WALK; polls = 0;
-                    break;
-                }
-                cur = (int)w.x;
-                break;
-            }
-            if (state == S_POP) {
-                // one vertex of the loop popx -> ... -> head: pop count + 1, free
-                if (bad(cur) || bad(popx)) break;
-                const uint4 w = ld4(W + cur);
-                if ((int)w.z != path || ++walked > n) { fail(6); break; }
-                const uint4 nw = make_uint4(P_NONE, w.y + 1u, O_FREE, 0u);
-                const uint4 old = cas4(W + cur, w, nw);
-                if (!same(old, w)) break;   // a flag arrived: again
-                progress();
-                if (w.w & F_ATT) push(wake, &wk_t, &wk_h, 2 * n, cur);
-                if (cur == head) {
-                    // popx gets its next successor and becomes the head
-                    int64_t rb; uint32_t deg;
-                    row_bounds<OFF64>(g, popx, rb, deg);
-                    const Ctr4 o = philox4x32_10(Ctr4{kx, (uint32_t)popx, tree, 0u}, k0, k1);
-                    const uint32_t j = __umulhi(o.x, deg);
-                    int px;
-                    if (WT) { const WArc arc = g.warc[rb + j]; px = (o.y < arc.thr) ? arc.col : arc.alias_col; }
-                    else px = __ldg(g.col + rb + j);
-                    for (int tries = 0;; ++tries) {
-                        const uint4 wp = ld4(W + popx);
-                        const uint4 np = make_uint4((uint32_t)px, kx, (uint32_t)path, wp.w);
-                        if (same(cas4(W + popx, wp, np), wp)) break;
-                        if (tries > 1000) { fail(7); break; }
-                    }
-                    head = popx; hp = px;
-                    state = S_WALK;
-                } else {
-                    cur = (int)w.x;
-                }
-                break;
-            }
-            if (state == S_SET) {
-                // one vertex of the path start -> head joins the tree
-                if (bad(cur)) break;
-                const uint4 w = ld4(W + cur);
-                if ((int)w.z != path || ++walked > n) { fail(8); break; }
-                const uint4 nw = make_uint4(w.x, w.y, O_SET, 0u);
-                if (!same(cas4(W + cur, w, nw), w)) break;
-                progress();
-                if (w.w & F_ATT) push(wake, &wk_t, &wk_h, 2 * n, cur);
-                if ((int)w.x == hp) { die(); break; }
-                cur = (int)w.x;
-                break;
-            }
-            // ---- S_WALK: one step of the loop-erased walk
-            const int a = head == -1 ? start : hp;
-            if (bad(a)) break;
-            const uint4 w = ld4(W + a);
+            if (la >= 0 && bad(la)) continue;
+            uint4 w = make_uint4(0, 0, 0, 0);
+            int ai = 0;
+            int64_t rb = 0;
+            uint32_t deg = 0;
+            if (la >= 0) w = ld4(W + la);
+            if (aux) ai = ldi(aux);
+            if (rowv >= 0) row_bounds<OFF64>(g, rowv, rb, deg);
+
+            // ---------------- phase C: decide; at most one 16-byte CAS and
+            // one int CAS, issued together in phase D
+            uint4 *c_a = nullptr; uint4 c_cmp = w, c_val = w;   // 16-byte CAS (claims)
+            uint4 *s_a = nullptr; uint4 s_val = w;              // 16-byte store (owner's writes)
+            int *i_a = nullptr; int i_cmp = 0, i_val = 0;       // int CAS
+            int dv = -1;                  // vertex to draw a successor for (claim)
+            int after = 0;                // what phase E does with the outcome
             const uint32_t o = w.z;
-            if (head != -1 && o != O_SET && (int)o != path && vread(&k_v[me]) == path) {
-                // an earlier walk asked for vertex k_x: hand the suffix from
-                // there over (the head's successor lies outside the path)
-                kw = vread(&k_w[me]);
-                k_v[me] = -1;
-                // commit only while the asker still waits for this path; its
-                // request fields are then fixed
-                if (kw >= 0 && kw < (int)blockDim.x && atomicCAS(&wait_for[kw], path, HAND_BUSY) == path) {
-                    const int x = vread(&req_x[kw]);
-                    kp = vread(&req_p[kw]);
-                    if (bad(x)) break;
-                    const uint4 wx = ld4(W + x);
-                    if ((int)wx.z == path && kp >= 0 && kp < path) {
-                        cur = x; end = x; walked = 0; hp = a;
-                        state = S_HAND;
+            switch (state) {
+                case S_WALK: {
+                    const int a = la;
+                    if (head != -1 && o != O_SET && (int)o != path && vread(&k_v[me]) == path) {
+                        // an earlier walk asked for a vertex of this path: at
+                        // this clean point (the successor lies outside the
+                        // path) commit, if the asker still waits
+                        const int kw2 = vread(&k_w[me]);
+                        k_v[me] = -1;
+                        if (kw2 >= 0 && kw2 < (int)blockDim.x &&
+                            atomicCAS(&wait_for[kw2], path, HAND_BUSY) == path) {
+                            const int x = vread(&req_x[kw2]);
+                            kp = vread(&req_p[kw2]);
+                            if (!bad(x) && kp >= 0 && kp < path) {
+                                cur = x; end = x; walked = 0; qv = kw2;   // qv: the asker's walker
+                                state = S_HAND;     // x's ownership is checked on its load
+                                break;
+                            }
+                            *(volatile int *)&wait_for[kw2] = path;   // give it back
+                        }
+                    }
+                    if (o == O_SET) {
+                        if (head == -1) { path = -1; state = S_IDLE; }   // the start is in the tree
+                        else { cur = start; walked = 0; state = S_SET; }
+                    } else if ((int)o == path) {
+                        // a -> ... -> head -> a is a cycle: pop it, a last
+                        kx = w.y + 1u; popx = a; cur = (int)w.x; walked = 1;
+                        state = S_POP;
+                    } else if (o == O_FREE) {
+                        c_a = W + a; c_cmp = w; c_val = make_uint4(w.x, w.y, (uint32_t)path, 0u);
+                        if (w.x == P_NONE) dv = a;
+                        after = 1;
+                    } else if (head == -1) {
+                        // the start lies on another path: look again later
+                        push(retry, &rq_t, &rq_h, nstart, path);
+                        path = -1; state = S_IDLE;
+                    } else if ((int)o < path) {
+                        begin_hang(path, a, S_IDLE);   // an earlier path: hang here
+                    } else {
+                        aq = (int)o; state = S_QCHK;   // a later path: look at its status
+                    }
+                    break;
+                }
+                case S_QCHK: {
+                    // the later path aq owns hp: take its suffix over if it is
+                    // parked, else ask its walker to hand it over
+                    if ((int)o != aq) { state = S_WALK; break; }
+                    if (ai == PS_PARKED || ai == PS_RESUMABLE) {
+                        i_a = pstat + aq; i_cmp = ai; i_val = PS_ADOPTING; after = 6;
+                    } else {
+                        cur = hp; state = S_WAITK; polls = 0;
+                        *(volatile int *)&req_x[me] = hp;
+                        *(volatile int *)&req_p[me] = path;
+                        __threadfence_block();
+                        *(volatile int *)&wait_for[me] = aq;
+                    }
+                    break;
+                }
+                case S_ADPREP: {
+                    // holding aq ADOPTING: hp must still be aq's (it may have
+                    // run and parked again since), else give aq back
+                    if ((int)o != aq) { begin_hang(aq, ai, S_WALK); break; }
+                    qv = hp; cur = hp; end = ai; walked = 0; state = S_ADOPT;
+                    break;
+                }
+                case S_WAITK: {
+                    if ((int)o != aq || ai == PS_PARKED || ai == PS_RESUMABLE) {
+                        // the situation changed: withdraw, unless aq has just
+                        // committed to hand over (then wait for the mailbox)
+                        if (atomicCAS(&wait_for[me], aq, -1) == aq) { state = S_WALK; polls = 0; }
                         break;
                     }
-                    *(volatile int *)&wait_for[kw] = path;   // not ours any more: the asker looks again
+                    if (ai >= PS_ACTIVE) {
+                        const int vw = ai - PS_ACTIVE;
+                        const int other = vread(&k_w[vw]);
+                        if (vread(&k_v[vw]) != aq || other < 0 || other >= (int)blockDim.x ||
+                            vread(&req_p[other]) > path) {
+                            *(volatile int *)&k_w[vw] = me;
+                            __threadfence_block();
+                            *(volatile int *)&k_v[vw] = aq;
+                        }
+                    }
+                    waited_out();
+                    break;
                 }
-            }
-            if (o == O_SET) {
-                if (head == -1) { path = -1; state = S_IDLE; break; }   // start already in the tree
-                cur = start; walked = 0; state = S_SET;
-                break;
-            }
-            if ((int)o == path) {
-                // a -> ... -> head -> a is a cycle: pop it (a first, at the end)
-                kx = w.y + 1u; popx = a; cur = (int)w.x; walked = 1;
-                state = S_POP;
-                break;
-            }
-            if (o == O_FREE) {
-                uint4 nw = w;
-                nw.z = (uint32_t)path;
-                if (w.x == P_NONE) {
-                    int64_t rb; uint32_t deg;
-                    row_bounds<OFF64>(g, a, rb, deg);
-                    const Ctr4 r = philox4x32_10(Ctr4{w.y, (uint32_t)a, tree, 0u}, k0, k1);
-                    const uint32_t j = __umulhi(r.x, deg);
-                    if (WT) { const WArc arc = g.warc[rb + j]; nw.x = (uint32_t)((r.y < arc.thr) ? arc.col : arc.alias_col); }
-                    else nw.x = (uint32_t)__ldg(g.col + rb + j);
+                case S_HAND: {
+                    // hand cur .. head over to path kp
+                    if ((int)o != path || ++walked > n) {
+                        if (cur == end && walked <= 1) {
+                            // the asked vertex left this path: the asker looks again
+                            *(volatile int *)&wait_for[qv] = path;
+                            walked = 0; state = S_WALK;
+                        } else fail(4);
+                        break;
+                    }
+                    s_a = W + cur; s_val = make_uint4(w.x, w.y, (uint32_t)kp, 0u);
+                    after = 4;
+                    break;
                 }
-                if (!same(cas4(W + a, w, nw), w)) break;   // lost a race: look again
-                progress();
-                if (head == -1) {
-                    sti(pstat + path, PS_ACTIVE + me);
-                    atomicAdd(&sh_live, 1);
+                case S_ADOPT: {
+                    if ((int)o != aq || ++walked > n) { fail(5); break; }
+                    s_a = W + cur; s_val = make_uint4(w.x, w.y, (uint32_t)path, 0u);
+                    after = 5;
+                    break;
                 }
-                head = a; hp = (int)nw.x;
-                break;
+                case S_POP: {
+                    if ((int)o != path || ++walked > n) { fail(6); break; }
+                    s_a = W + cur; s_val = make_uint4(P_NONE, w.y + 1u, O_FREE, 0u);
+                    after = 2;
+                    break;
+                }
+                case S_POPX: {
+                    if ((int)o != path) { fail(7); break; }
+                    // popx gets its next successor (drawn into hp last tick) and
+                    // becomes the head
+                    s_a = W + popx; s_val = make_uint4((uint32_t)hp, kx, (uint32_t)path, 0u);
+                    after = 7;
+                    break;
+                }
+                case S_SET: {
+                    if ((int)o != path || ++walked > n) { fail(8); break; }
+                    s_a = W + cur; s_val = make_uint4(w.x, w.y, O_SET, 0u);
+                    after = 3;
+                    break;
+                }
+                case S_HANG: {
+                    // the flag is on hg_a (set before this load): if hg_a is
+                    // still an earlier path's, its owner will see the flag when
+                    // it settles or frees hg_a; else hg_p looks again itself
+                    if (!is_path(o) || (int)o >= hg_p) {
+                        i_a = pstat + hg_p; i_cmp = PS_PARKING; i_val = PS_RESUMABLE; after = 9;
+                    } else {
+                        i_a = pstat + hg_p; i_cmp = PS_PARKING; i_val = PS_PARKED; after = 8;
+                    }
+                    break;
+                }
+                case S_WAKE: {
+                    // neighbour wv of the woken vertex qv: a parked head there
+                    // pointing at qv is made resumable
+                    if (wv >= 0 && is_path(o) && (int)w.x == qv) {
+                        const int p = (int)o;
+                        i_a = pstat + p; i_cmp = PS_PARKED; i_val = PS_RESUMABLE; after = 10;
+                    }
+                    if (wj < (int)degx) { wv = ai; ++wj; }
+                    else if (!i_a) state = S_IDLE;
+                    else wj = (int)degx + 1;   // finish after this CAS
+                    break;
+                }
+                default: break;
             }
-            // a lies on another path q
-            const int q = (int)o;
-            if (head == -1) {
-                // the start lies on another path: look again later
-                push(retry, &rq_t, &rq_h, nstart, path);
-                path = -1; state = S_IDLE;
-                break;
+
+            // ---------------- phase D: the tick's atomics, issued together
+            uint4 c_old = c_cmp;
+            int i_old = i_cmp;
+            int px = -1;
+            if (c_a) c_old = cas4(c_a, c_cmp, c_val);
+            if (s_a) st4(s_a, s_val);
+            if (i_a) i_old = atomicCAS(i_a, i_cmp, i_val);
+            if (dv >= 0) px = draw(dv, w.y, rb, deg);   // the arc load overlaps the CAS
+            const bool c_ok = c_a && same(c_old, c_cmp);
+            const bool i_ok = i_a && i_old == i_cmp;
+
+            // ---------------- phase E: outcomes
+            switch (after) {
+                case 1:   // claim
+                    if (!c_ok) break;   // lost a race: look again
+                    progress();
+                    if (head == -1) { sti(pstat + path, PS_ACTIVE + me); atomicAdd(&sh_live, 1); }
+                    head = la;
+                    if (dv >= 0) {
+                        st4(W + la, make_uint4((uint32_t)px, w.y, (uint32_t)path, 0u));
+                        hp = px;
+                    } else {
+                        hp = (int)w.x;
+                    }
+                    break;
+                case 2:   // pop
+                    progress();
+                    release_flag(cur);
+                    if (cur == head) {
+                        rbx = rb; degx = deg;
+                        hp = draw(popx, kx, rbx, degx);
+                        state = S_POPX;
+                    } else {
+                        cur = (int)w.x;
+                    }
+                    break;
+                case 7:   // popx's new successor
+                    head = popx;   // hp holds the successor
+                    state = S_WALK;
+                    break;
+                case 3:   // settle
+                    progress();
+                    release_flag(cur);
+                    if ((int)w.x == hp) die();
+                    else cur = (int)w.x;
+                    break;
+                case 4:   // hand over one vertex
+                    progress();
+                    if ((int)w.x == hp) {
+                        // cur was the head: post the mailbox, hang the prefix
+                        mb_h[qv] = cur; mb_p[qv] = hp;
+                        __threadfence_block();
+                        *(volatile int *)&mb_ok[qv] = 1;
+                        if (end == start) {
+                            // the whole path moved, start included: look at
+                            // the start again later (a later pop could free it)
+                            push(retry, &rq_t, &rq_h, nstart, path);
+                            die();
+                        } else {
+                            begin_hang(path, end, S_IDLE);
+                        }
+                    } else {
+                        cur = (int)w.x;
+                    }
+                    break;
+                case 5:   // take one vertex over
+                    progress();
+                    if ((int)w.x == end) {
+                        head = cur; hp = end;
+                        // aq keeps its prefix, now hanging at the first vertex taken
+                        if (s.order[aq] == qv) {
+                            sti(pstat + aq, PS_DEAD);
+                            atomicSub(&sh_live, 1);
+                            push(retry, &rq_t, &rq_h, nstart, aq);
+                            state = S_WALK;
+                        } else {
+                            begin_hang(aq, qv, S_WALK);
+                        }
+                    } else {
+                        cur = (int)w.x;
+                    }
+                    break;
+                case 6:   // won aq's status: check hp is still aq's
+                    if (i_ok) state = S_ADPREP;
+                    else state = S_WALK;
+                    break;
+                case 8:   // parked (or a waker came first and queued hg_p)
+                    if (hg_p == path && hg_next == S_IDLE) path = -1;
+                    state = hg_next; polls = 0;
+                    if (state == S_IDLE) head = -1;
+                    break;
+                case 9:   // hg_p could not hang: make it resumable
+                    if (i_ok) push(resume, &rs_t, &rs_h, 2 * nstart, hg_p);
+                    if (hg_p == path && hg_next == S_IDLE) path = -1;
+                    state = hg_next; polls = 0;
+                    if (state == S_IDLE) head = -1;
+                    break;
+                case 10:  // a parked head at the woken vertex
+                    if (i_ok) push(resume, &rs_t, &rs_h, 2 * nstart, (int)o);
+                    else if (i_old == PS_PARKING && atomicCAS(pstat + (int)o, PS_PARKING, PS_RESUMABLE) == PS_PARKING)
+                        push(resume, &rs_t, &rs_h, 2 * nstart, (int)o);
+                    if (wj > (int)degx) state = S_IDLE;
+                    break;
+                default: break;
             }
-            if (q < path) {
-                // q is earlier: park this path at a
-                if (hang(path, a)) { path = -1; head = -1; state = S_IDLE; polls = 0; }
-                else { path = -1; head = -1; state = S_IDLE; polls = 0; }
-                break;
-            }
-            // q is later: take its suffix from a over
-            const int st = ldi(pstat + q);
-            if ((st == PS_PARKED || st == PS_RESUMABLE) && atomicCAS(pstat + q, st, PS_ADOPTING) == st) {
-                // q may have run and parked again since a was read (the same
-                // status twice): a must still be q's, else give q back
-                __threadfence_block();
-                if ((int)ld4(W + a).z != q) { hang(q, ldi(patt + q)); break; }
-                aq = q; qv = a; cur = a; end = ldi(patt + q); walked = 0;
-                state = S_ADOPT;
-                break;
-            }
-            aq = q; cur = a; state = S_WAITK; polls = 0;
-            *(volatile int *)&req_x[me] = a;
-            *(volatile int *)&req_p[me] = path;
-            __threadfence_block();
-            *(volatile int *)&wait_for[me] = q;
-            } while (0);
         }
         __syncthreads();
         if (me == 0 && sh_err) atomicOr(s.err, sh_err);
@@ -576,7 +670,8 @@ rwc_status sample_park(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, do
     const int32_t *order = nullptr;
     RWC_TRY(walker_order(G, &order));
     // per tree: 16 n (words) + 4 (n-1) x 5 (status, hang point, retry, resume x 2) + 8 n (wake)
-    const size_t per_tree = (size_t)n * 16 + (size_t)(n - 1) * 20 + (size_t)n * 8 + 1024;
+    // + 4 n (flags)
+    const size_t per_tree = (size_t)n * 16 + (size_t)(n - 1) * 20 + (size_t)n * 12 + 1024;
     int64_t B = o.trees_per_chunk;
     if (B <= 0) {
         size_t fr = 0, tot = 0;
@@ -591,7 +686,8 @@ rwc_status sample_park(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, do
     const size_t a_word = ((size_t)B * n * 16 + 255) & ~(size_t)255;
     const size_t a_int = ((size_t)B * (n - 1) * 4 + 255) & ~(size_t)255;
     const size_t a_wake = ((size_t)B * n * 8 + 255) & ~(size_t)255;
-    const size_t bytes = a_word + 5 * a_int + a_wake + 256;
+    const size_t a_flag = ((size_t)B * n * 4 + 255) & ~(size_t)255;
+    const size_t bytes = a_word + 5 * a_int + a_wake + a_flag + 256;
     RWC_CUDA_TRY(cudaMallocAsync(&buf, bytes, stream));
     struct Free {
         void *p; cudaStream_t s;
@@ -605,6 +701,7 @@ rwc_status sample_park(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, do
     ps.retry = (int *)q; q += a_int;
     ps.resume = (int *)q; q += 2 * a_int;
     ps.wake = (int *)q; q += a_wake;
+    ps.flag = (int *)q; q += a_flag;
     char *tail = q;
     ps.order = order;
     ps.err = (int *)tail;
@@ -627,6 +724,7 @@ rwc_status sample_park(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, do
         RWC_CUDA_TRY(cudaMemsetAsync(ps.retry, 0, (size_t)Bc * (n - 1) * 4, stream));
         RWC_CUDA_TRY(cudaMemsetAsync(ps.resume, 0, (size_t)Bc * (n - 1) * 8, stream));
         RWC_CUDA_TRY(cudaMemsetAsync(ps.wake, 0, (size_t)Bc * n * 8, stream));
+        RWC_CUDA_TRY(cudaMemsetAsync(ps.flag, 0, (size_t)Bc * n * 4, stream));
         if (prof) cudaEventRecord(ev[0], stream);
         ::rwc::count_launches(1);
         p_init<<<sms * 8, 256, 0, stream>>>(n, g.root, ps.word, ps.pstat, Bc);

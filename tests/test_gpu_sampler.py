@@ -51,7 +51,10 @@ MODES = {"shared": rwc.Options(mode=rwc.MODE_SHARED),
          "walker_yield": rwc.Options(mode=rwc.MODE_WALKER, walker_policy=1),
          "walker_yield_w32": rwc.Options(mode=rwc.MODE_WALKER, walker_policy=1, block_threads=32),
          "walker_fresh": rwc.Options(mode=rwc.MODE_WALKER, walker_policy=3),
-         "walker_fresh_w32": rwc.Options(mode=rwc.MODE_WALKER, walker_policy=3, block_threads=32)}
+         "walker_fresh_w32": rwc.Options(mode=rwc.MODE_WALKER, walker_policy=3, block_threads=32),
+         "walker_park": rwc.Options(mode=rwc.MODE_WALKER, walker_policy=4, max_wait_ns=5_000_000_000),
+         "walker_park_chunk4": rwc.Options(mode=rwc.MODE_WALKER, walker_policy=4, trees_per_chunk=4,
+                                           max_wait_ns=5_000_000_000)}
 
 
 @pytest.mark.parametrize("mode", list(MODES))
@@ -61,7 +64,7 @@ def test_special_graphs_bit_exact(gname, mode):
 
 
 @pytest.mark.parametrize("mode", ["shared", "global", "global_chunk3", "walker", "walker_w32_chunk5",
-                                  "walker_fresh"])
+                                  "walker_fresh", "walker_park"])
 def test_small_ba_config_bit_exact(mode):
     """BA n=2000, 3 edges per node + Hamiltonian path, unit weights, 1000
     trees, Philox seed 1: every tree identical to the oracle's."""
@@ -73,11 +76,11 @@ def test_small_ba_config_bit_exact(mode):
 
 
 @pytest.mark.parametrize("mode", ["global", "global_nojump", "walker", "walker_w64", "walker_yield",
-                                  "walker_wait", "walker_fresh"])
+                                  "walker_wait", "walker_fresh", "walker_park"])
 def test_grid_several_chunks_bit_exact(mode):
     g = synth.grid2d(61, 67)
     if mode.startswith("walker"):
-        pol = {"walker_yield": 1, "walker_wait": 2, "walker_fresh": 3}.get(mode, 0)
+        pol = {"walker_yield": 1, "walker_wait": 2, "walker_fresh": 3, "walker_park": 4}.get(mode, 0)
         opt = rwc.Options(mode=rwc.MODE_WALKER, trees_per_chunk=9,
                           block_threads=64 if mode == "walker_w64" else 0, walker_policy=pol)
     else:
@@ -92,6 +95,7 @@ def test_weighted_rmat_int64_offsets_bit_exact():
     assert_exact(g, 8, rwc.Options(mode=rwc.MODE_GLOBAL))
     assert_exact(g, 16, rwc.Options(mode=rwc.MODE_WALKER), flags=rwc.GRAPH_INT64_OFFSETS)
     assert_exact(g, 16, rwc.Options(mode=rwc.MODE_WALKER, block_threads=128))
+    assert_exact(g, 16, rwc.Options(mode=rwc.MODE_WALKER, walker_policy=4), flags=rwc.GRAPH_INT64_OFFSETS)
 
 
 def test_weighted_rgg_shared_bit_exact():
@@ -108,6 +112,7 @@ def test_tree_offset_and_shards_add_up():
     assert torch.equal(a, b)
     assert_exact(g, 10, rwc.Options(mode=rwc.MODE_GLOBAL), seed=9, tree0=4000000000)
     assert_exact(g, 10, rwc.Options(mode=rwc.MODE_WALKER), seed=9, tree0=4000000000)
+    assert_exact(g, 10, rwc.Options(mode=rwc.MODE_WALKER, walker_policy=4), seed=9, tree0=4000000000)
 
 
 def test_seed_high_bits_matter():
@@ -232,7 +237,7 @@ def test_graph_create_pivot_is_oracle_max_degree_root(weighted):
 
 
 @pytest.mark.parametrize("weighted", [False, True])
-@pytest.mark.parametrize("mode", ["shared", "global", "walker"])
+@pytest.mark.parametrize("mode", ["shared", "global", "walker", "walker_park"])
 def test_parallel_arcs_bit_exact(mode, weighted):
     g = multigraph(weighted)
     assert (np.diff(g.col)[np.diff(g.src()) == 0] == 0).any()   # some parallel arcs
