@@ -298,6 +298,28 @@ static rwc_status create_impl(int64_t n, int64_t nnz, const int64_t *rp, const i
             g.hc_n = (int64_t)crow.size(); g.hc_row = pr; g.hc_beg = pb; g.hfirst = ph;
         }
     }
+    {
+        // rows of at most HEAVY_DEG arcs by degree bin (2, 4, 8, 16, more arcs)
+        std::vector<int32_t> bins[5];
+        for (int64_t u = 0; u < n; ++u) {
+            const int64_t deg = rp[u + 1] - rp[u];
+            if (deg > HEAVY_DEG) continue;
+            const int b = deg <= 2 ? 0 : deg <= 4 ? 1 : deg <= 8 ? 2 : deg <= 16 ? 3 : 4;
+            bins[b].push_back((int32_t)u);
+        }
+        std::vector<int32_t> all;
+        all.reserve((size_t)n);
+        for (int b = 0; b < 5; ++b) {
+            g.bin_off[b] = (int64_t)all.size();
+            all.insert(all.end(), bins[b].begin(), bins[b].end());
+        }
+        g.bin_off[5] = (int64_t)all.size();
+        if (!all.empty()) {
+            int32_t *pbr;
+            if ((e = upload(G, &pbr, all.data(), all.size())) != cudaSuccess) return fail(e, "degree bins");
+            g.bin_rows = pbr;
+        }
+    }
     if ((e = cudaMallocHost((void **)&G->host_scalars, 64 * sizeof(int64_t))) != cudaSuccess)
         return fail(e, "pinned scalars");
     *out = G;

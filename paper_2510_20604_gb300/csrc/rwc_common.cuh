@@ -62,6 +62,11 @@ struct DevGraph {
     const int32_t *hc_row = nullptr; // [hc_n] row of each chunk (a row's chunks are consecutive)
     const int64_t *hc_beg = nullptr; // [hc_n] first arc of each chunk
     const int32_t *hfirst = nullptr; // [n] first chunk of a heavy row, -1 for other rows
+    // the other rows grouped by degree for the sparse products: bin b (b = 0..4)
+    // holds the rows of at most 2^(b+1) arcs (more than 16 for b = 4), each
+    // read by 2^(b+1) lanes; rows bin_rows[bin_off[b] .. bin_off[b+1])
+    const int32_t *bin_rows = nullptr;
+    int64_t bin_off[6] = {0, 0, 0, 0, 0, 0};
 };
 
 constexpr int64_t HEAVY_DEG = 1024;

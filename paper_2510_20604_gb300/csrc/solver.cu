@@ -384,6 +384,39 @@ __global__ void inner_update(int64_t n, int k, const double *rz, const double *p
     }
 }
 
+// q = L p over the rows of degree bin VW (rows of at most VW arcs, or more
+// than 16 arcs for VW = 32), VW lanes per row; all lanes of a warp iterate
+// together so the shuffles stay converged.  Returns this thread's share of
+// <p, q>.
+template <int VW, bool OFF64, bool W>
+__device__ __forceinline__ double spmv_bin(const DevGraph &g, const int32_t *__restrict__ rows,
+                                           int64_t nrows_bin, const float *__restrict__ p,
+                                           float *__restrict__ q, int64_t tid, int64_t nthr) {
+    const int sub = threadIdx.x & (VW - 1);
+    const int64_t row0 = tid / VW, ngroups = nthr / VW;
+    double acc = 0.0;
+    for (int64_t i0 = row0 - (row0 % (32 / VW)); i0 < nrows_bin; i0 += ngroups) {
+        const int64_t i = i0 + (row0 % (32 / VW));
+        float sacc = 0.f;
+        int u = -1;
+        if (i < nrows_bin) {
+            u = rows[i];
+            int64_t b, e2;
+            rowb<OFF64>(g, u, b, e2);
+            for (int64_t j = b + sub; j < e2; j += VW) sacc += (W ? g.w[j] : 1.f) * p[g.col[j]];
+        }
+#pragma unroll
+        for (int o = VW / 2; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o, VW);
+        if (sub == 0 && u >= 0) {
+            const float pu = p[u];
+            const float qu = (float)g.d[u] * pu - sacc;
+            q[u] = qu;
+            acc += (double)pu * (double)qu;
+        }
+    }
+    return acc;
+}
+
 // Grid-wide sums in a fixed order inside a cooperative launch: every block
 // stores its block_sum_fixed in parts, the grid synchronises, and every block
 // adds all the parts in block order, so all blocks hold the same bits.  The
@@ -445,6 +478,14 @@ __global__ void __launch_bounds__(TPB) cg1_coop(DevGraph g, const float *__restr
     for (; it < max_it; ++it) {
         // q = L p and <p, q>
         double acc = 0.0;
+        if (g.bin_rows) {
+            // rows by degree bin, each bin with as many lanes per row as its degrees
+            acc += spmv_bin<2, OFF64, W>(g, g.bin_rows + g.bin_off[0], g.bin_off[1] - g.bin_off[0], p, q, tid, nthr);
+            acc += spmv_bin<4, OFF64, W>(g, g.bin_rows + g.bin_off[1], g.bin_off[2] - g.bin_off[1], p, q, tid, nthr);
+            acc += spmv_bin<8, OFF64, W>(g, g.bin_rows + g.bin_off[2], g.bin_off[3] - g.bin_off[2], p, q, tid, nthr);
+            acc += spmv_bin<16, OFF64, W>(g, g.bin_rows + g.bin_off[3], g.bin_off[4] - g.bin_off[3], p, q, tid, nthr);
+            acc += spmv_bin<32, OFF64, W>(g, g.bin_rows + g.bin_off[4], g.bin_off[5] - g.bin_off[4], p, q, tid, nthr);
+        } else
         for (int64_t u0 = row0 - (row0 % (32 / VW)); u0 < g.n; u0 += nrows) {
             const int64_t u = u0 + (row0 % (32 / VW));
             float sacc = 0.f;
