@@ -116,7 +116,7 @@ def code_hash(path, begin=None, end=None):
 
 
 # the walker kernel's source region in walker.cu (what a traffic capture measured)
-W_TREES_REGION = ("walker.cu", "__global__ void __maxnreg__(RWC_WALKER_MAXNREG) w_trees(",
+W_TREES_REGION = ("walker.cu", "struct DrawRow {",
                   "// visits_u = k_u + 1 over the chunk's trees")
 
 

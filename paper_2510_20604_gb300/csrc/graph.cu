@@ -320,6 +320,21 @@ static rwc_status create_impl(int64_t n, int64_t nnz, const int64_t *rp, const i
             g.bin_rows = pbr;
         }
     }
+    if (!w && !g.off64) {
+        // inline neighbour lists for bounded-degree graphs (grids, meshes)
+        int64_t maxdeg = 0;
+        for (int64_t u = 0; u < n; ++u) maxdeg = std::max<int64_t>(maxdeg, rp[u + 1] - rp[u]);
+        const int ew = maxdeg <= 4 ? 4 : maxdeg <= 8 ? 8 : 0;
+        if (ew) {
+            std::vector<int32_t> rows((size_t)n * ew, -1);
+            for (int64_t u = 0; u < n; ++u)
+                for (int64_t j = rp[u]; j < rp[u + 1]; ++j) rows[(size_t)u * ew + (j - rp[u])] = col[j];
+            int32_t *pe;
+            if ((e = upload(G, &pe, rows.data(), rows.size())) != cudaSuccess) return fail(e, "inline rows");
+            g.ell = reinterpret_cast<const int4 *>(pe);
+            g.ell_w = ew;
+        }
+    }
     if ((e = cudaMallocHost((void **)&G->host_scalars, 64 * sizeof(int64_t))) != cudaSuccess)
         return fail(e, "pinned scalars");
     *out = G;

@@ -67,6 +67,11 @@ struct DevGraph {
     // read by 2^(b+1) lanes; rows bin_rows[bin_off[b] .. bin_off[b+1])
     const int32_t *bin_rows = nullptr;
     int64_t bin_off[6] = {0, 0, 0, 0, 0, 0};
+    // unweighted graphs with int32 offsets whose degrees are all at most 8:
+    // every row's heads inline, ell_w (4 or 8) slots per vertex in arc order,
+    // -1 after the last (0 = none)
+    const int4 *ell = nullptr;
+    int ell_w = 0;
 };
 
 constexpr int64_t HEAVY_DEG = 1024;

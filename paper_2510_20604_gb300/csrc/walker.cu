@@ -31,6 +31,7 @@
 #include <cstring>
 #include <numeric>
 #include <random>
+#include <type_traits>
 #include <vector>
 
 #include "rwc_common.cuh"
@@ -114,21 +115,65 @@ __device__ __forceinline__ uint64_t gtimer() {
 
 // Walker states.  Each loop iteration ("tick") does at most one vertex of
 // work per walker, and the memory accesses of all states are issued by the
-// same instructions: one load of a vertex word (with the row bounds of the
-// vertex that may be drawn), then the stores, the claim CAS and the
-// successor draw, whose arc load overlaps the CAS.  The lanes of a warp thus
-// pay about two dependent memory round trips per tick, whatever mix of
-// states they are in.  Waits poll shared memory or the one vertex word.
+// same instructions: one load of a vertex word (with the row of the vertex
+// that may be drawn), then the stores, the claim CAS and the successor draw,
+// whose arc load overlaps the CAS (on graphs of degree at most 8 the draw
+// picks from an inline row loaded beside the word, with no arc load).  The
+// lanes of a warp thus pay about two dependent memory round trips per tick,
+// whatever mix of states they are in.  Waits poll shared memory or the one
+// vertex word.  (Loading the next tick's word at the end of a tick, while a
+// claim is in flight, was measured slower on every graph: 29% on a 256² grid,
+// 43% on a 1024² grid, 24% on R-MAT 20.)
 enum : int { S_IDLE = 0, S_WALK, S_POP, S_REL, S_SET, S_WAITK, S_WAITV, S_WAITH, S_DONE };
 
-// Register cap of the walker kernel: 46 registers are used without spills.
-// (A cap of 40 lets 96-walker blocks keep 2000 trees resident, but its
-// spills cost more than the extra walkers gain.)
+// Register cap of the walker kernel: at most 56 registers are used without
+// spills (52 without inline rows of 8), which keeps 18 blocks of 64 walkers
+// per SM resident, 2736 trees on 152 SMs.  (A cap of 40 lets 96-walker blocks
+// keep 2000 trees resident, but its spills cost more than the extra walkers
+// gain.)
 #ifndef RWC_WALKER_MAXNREG
-#define RWC_WALKER_MAXNREG 48
+#define RWC_WALKER_MAXNREG 64
 #endif
 
-template <bool OFF64, bool WT, bool DIAG>
+// The row of a vertex that may be drawn: its CSR bounds (EW = 0), or, for
+// graphs whose degrees are at most EW (4 or 8), its inline neighbour list
+// (heads in arc order, -1 after the last), read with one or two 16-byte loads.
+template <bool OFF64, int EW>
+struct DrawRow {
+    int4 e[EW / 4];
+    __device__ __forceinline__ void load(const DevGraph &g, int32_t u) {
+#pragma unroll
+        for (int i = 0; i < EW / 4; ++i) e[i] = __ldg(g.ell + (int64_t)u * (EW / 4) + i);
+    }
+    // head of the arc picked by the 32-bit uniform x: arc floor(x deg / 2^32)
+    __device__ __forceinline__ int32_t pick(uint32_t x) const {
+        uint32_t deg = 0;
+#pragma unroll
+        for (int i = 0; i < EW / 4; ++i)
+            deg += (e[i].x >= 0) + (e[i].y >= 0) + (e[i].z >= 0) + (e[i].w >= 0);
+        const uint32_t j = __umulhi(x, deg);
+        const int4 q = (EW == 4 || j < 4) ? e[0] : e[EW / 4 - 1];
+        const uint32_t jj = j & 3u;
+        return jj < 2 ? (jj == 0 ? q.x : q.y) : (jj == 2 ? q.z : q.w);
+    }
+};
+template <bool OFF64>
+struct DrawRow<OFF64, 0> {
+    int64_t rb;
+    uint32_t deg;
+    __device__ __forceinline__ void load(const DevGraph &g, int32_t u) { row_bounds<OFF64>(g, u, rb, deg); }
+    template <bool WT>
+    __device__ __forceinline__ int32_t pick_csr(const DevGraph &g, uint32_t x, uint32_t y) const {
+        const uint32_t j = __umulhi(x, deg);
+        if (WT) {
+            const WArc arc = g.warc[rb + j];
+            return (y < arc.thr) ? arc.col : arc.alias_col;
+        }
+        return __ldg(g.col + rb + j);
+    }
+};
+
+template <bool OFF64, bool WT, int EW, bool DIAG>
 __global__ void __maxnreg__(RWC_WALKER_MAXNREG) w_trees(DevGraph g, WState s, int64_t B, uint32_t tree0,
                                                 uint32_t k0, uint32_t k1, int64_t max_wait_ns,
                                                 int wait_policy) {
@@ -328,9 +373,8 @@ __global__ void __maxnreg__(RWC_WALKER_MAXNREG) w_trees(DevGraph g, WState s, in
             else if (state == S_POP && cur == head) dv = popx;
             if (a < 0) continue;
             const uint64_t w = ldv(st + a);
-            int64_t rb = 0;
-            uint32_t deg = 0;
-            if (dv >= 0) row_bounds<OFF64>(g, dv, rb, deg);
+            DrawRow<OFF64, EW> row;
+            if (dv >= 0) row.load(g, dv);
 
             // ---- decide: at most one store, one CAS and one draw
             int32_t s_v = -1;  uint64_t s_val = 0;               // store
@@ -445,13 +489,8 @@ __global__ void __maxnreg__(RWC_WALKER_MAXNREG) w_trees(DevGraph g, WState s, in
             int32_t px = -1;
             if (d_u >= 0) {
                 const Ctr4 o = philox4x32_10(Ctr4{d_k, (uint32_t)d_u, tree, 0u}, k0, k1);
-                const uint32_t j = __umulhi(o.x, deg);
-                if (WT) {
-                    const WArc arc = g.warc[rb + j];
-                    px = (o.y < arc.thr) ? arc.col : arc.alias_col;
-                } else {
-                    px = __ldg(g.col + rb + j);
-                }
+                if constexpr (EW > 0) px = row.pick(o.x);
+                else px = row.template pick_csr<WT>(g, o.x, o.y);
             }
             if (after == 1) {
                 if (old == c_cmp) {
@@ -516,14 +555,19 @@ __global__ void w_accum(int64_t n, int32_t root, const uint64_t *word, int64_t B
 // one uint64 array (24 W bytes keep it 8-byte aligned).
 inline size_t walker_smem(int W) { return (size_t)W * (6 * sizeof(int) + 8); }
 
+template <int V> using int_c = std::integral_constant<int, V>;
+
+// f(off64, weighted, inline row width) as compile-time constants
 template <class F>
 void dispatch(const DevGraph &g, F f) {
     if (g.off64) {
-        if (g.weighted) f(std::true_type{}, std::true_type{});
-        else f(std::true_type{}, std::false_type{});
+        if (g.weighted) f(std::true_type{}, std::true_type{}, int_c<0>{});
+        else f(std::true_type{}, std::false_type{}, int_c<0>{});
     } else {
-        if (g.weighted) f(std::false_type{}, std::true_type{});
-        else f(std::false_type{}, std::false_type{});
+        if (g.weighted) f(std::false_type{}, std::true_type{}, int_c<0>{});
+        else if (g.ell_w == 4) f(std::false_type{}, std::false_type{}, int_c<4>{});
+        else if (g.ell_w == 8) f(std::false_type{}, std::false_type{}, int_c<8>{});
+        else f(std::false_type{}, std::false_type{}, int_c<0>{});
     }
 }
 
@@ -610,9 +654,10 @@ rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, 
         w_init<<<sms * 8, 256, 0, stream>>>(n, g.root, ws.word, Bc);
         if (prof) cudaEventRecord(ev[1], stream);
         rwc_status status = RWC_OK;
-        dispatch(g, [&](auto off64, auto wt) {
-            auto kern = (o.profile >= 2) ? w_trees<decltype(off64)::value, decltype(wt)::value, true>
-                                         : w_trees<decltype(off64)::value, decltype(wt)::value, false>;
+        dispatch(g, [&](auto off64, auto wt, auto ew) {
+            constexpr bool O = decltype(off64)::value, WT = decltype(wt)::value;
+            constexpr int EW = decltype(ew)::value;
+            auto kern = (o.profile >= 2) ? w_trees<O, WT, EW, true> : w_trees<O, WT, EW, false>;
             int Wc = W, per_sm = 0;
             if (Wc == 0) {
                 // largest multiple of 32 in [64, 512] whose resident blocks cover
@@ -796,8 +841,8 @@ extern "C" rwc_status rwc_sample_trees_noalloc(rwc_graph_t *G, uint64_t seed, in
         ::rwc::count_launches(1);
         w_init<<<sms * 8, 256, 0, stream>>>(n, g.root, ws.word, Bc);
         rwc_status status = RWC_OK;
-        dispatch(g, [&](auto off64, auto wt) {
-            auto kern = w_trees<decltype(off64)::value, decltype(wt)::value, false>;
+        dispatch(g, [&](auto off64, auto wt, auto ew) {
+            auto kern = w_trees<decltype(off64)::value, decltype(wt)::value, decltype(ew)::value, false>;
             const size_t smem = walker_smem(W);
             int per_sm = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, W, smem);

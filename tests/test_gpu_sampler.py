@@ -89,6 +89,31 @@ def test_grid_several_chunks_bit_exact(mode):
     assert_exact(g, 23, opt, root=-1)
 
 
+def _king_graph(rows, cols):
+    # 8-neighbour grid: degrees 3 to 8, so the walker draws from inline rows of 8
+    ids = np.arange(rows * cols).reshape(rows, cols)
+    us, vs = [], []
+    for dr, dc in ((0, 1), (1, 0), (1, 1), (1, -1)):
+        r0, r1 = max(0, -dr), rows - max(0, dr)
+        c0, c1 = max(0, -dc), cols - max(0, dc)
+        us.append(ids[r0:r1, c0:c1].ravel())
+        vs.append(ids[r0 + dr:r1 + dr, c0 + dc:c1 + dc].ravel())
+    return synth.from_edges(rows * cols, np.concatenate(us), np.concatenate(vs), name="king")
+
+
+@pytest.mark.parametrize("mode", ["walker", "walker_w64", "walker_yield", "walker_fresh"])
+@pytest.mark.parametrize("gname", ["king", "grid", "cycle"])
+def test_bounded_degree_inline_rows_bit_exact(mode, gname):
+    # degree <= 4 (grid, cycle) and <= 8 (king graph): the walker's draws pick
+    # from inline neighbour rows; several chunks, many trees per chunk
+    g = {"king": lambda: _king_graph(45, 53), "grid": lambda: synth.grid2d(70, 41),
+         "cycle": lambda: synth.cycle(900)}[gname]()
+    pol = {"walker_yield": 1, "walker_fresh": 3}.get(mode, 0)
+    opt = rwc.Options(mode=rwc.MODE_WALKER, trees_per_chunk=13,
+                      block_threads=64 if mode == "walker_w64" else 0, walker_policy=pol)
+    assert_exact(g, 31, opt, root=-1)
+
+
 def test_weighted_rmat_int64_offsets_bit_exact():
     g = synth.rmat(12, 16, seed=3, sigma=1.0)
     assert_exact(g, 16, rwc.Options(mode=rwc.MODE_GLOBAL), flags=rwc.GRAPH_INT64_OFFSETS)
