@@ -187,6 +187,11 @@ __global__ void __maxnreg__(RWC_WALKER_MAXNREG) w_trees(DevGraph g, WState s, in
     __shared__ int sh_active;           // walkers holding a start
     __shared__ int sh_err;
     __shared__ unsigned sh_prog;        // rewritten by every walker that stores a vertex word
+    // claim locks of graphs with inline rows (below); all free between ticks
+    constexpr int NLOCK = 256;
+    __shared__ int sh_lock[EW > 0 ? NLOCK : 1];
+    if constexpr (EW > 0)
+        for (int i = threadIdx.x; i < NLOCK; i += blockDim.x) sh_lock[i] = 0;
     // prio[W], kill[W], killer[W], ver[W], killv[W], wprog[W] (24 W bytes), then wt0[W]
     extern __shared__ __align__(8) int sh[];
     int *prio = sh;
@@ -485,7 +490,30 @@ __global__ void __maxnreg__(RWC_WALKER_MAXNREG) w_trees(DevGraph g, WState s, in
             if (s_v >= 0 || c_v >= 0) *(volatile unsigned *)&sh_prog = (unsigned)clock();
             if (s_v >= 0) stv(st + s_v, s_val);
             uint64_t old = 0;
-            if (c_v >= 0) old = cas_cta(st + c_v, c_cmp, c_val);
+            if (c_v >= 0) {
+                if constexpr (EW > 0) {
+                    // bounded-degree graphs, whose step waits on the tick latency
+                    // of single trees: the claim takes a shared-memory lock (a
+                    // hash of the vertex), re-reads the word and stores the claim,
+                    // instead of an L2 round trip for a CAS (8% shorter ticks on a
+                    // 256² grid tree alone; on R-MAT under load the CAS is faster,
+                    // 11% on R-MAT 20).  A busy lock fails the claim, which is
+                    // retried next tick.  Every writer of a FREE word claims it
+                    // under the lock, so the re-read sees the last claim.
+                    int *lk = &sh_lock[((uint32_t)c_v * 0x9E3779B1u) >> 24];
+                    if (atomicCAS(lk, 0, 1) == 0) {
+                        __threadfence_block();
+                        old = ldv(st + c_v);
+                        if (old == c_cmp) stv(st + c_v, c_val);
+                        __threadfence_block();
+                        atomicExch(lk, 0);
+                    } else {
+                        old = ~c_cmp;
+                    }
+                } else {
+                    old = cas_cta(st + c_v, c_cmp, c_val);
+                }
+            }
             int32_t px = -1;
             if (d_u >= 0) {
                 const Ctr4 o = philox4x32_10(Ctr4{d_k, (uint32_t)d_u, tree, 0u}, k0, k1);
