@@ -90,12 +90,12 @@ def algorithmic_bytes(draws, trees, n, weighted, off64):
 # on (code_hash of the .cu file), else reported as null.
 TRAFFIC_PER_DRAW = {
     # family: (bytes per draw, case captured, source file, code hash of the kernel region)
-    "grid": (277.4, "grid 256x256, 2000 trees, 64 walkers per tree: one w_trees launch "
-                     "(588.9 GB over 2.123e9 draws)", "walker.cu",
-             "ec78c283b954dd69a2f710758762f74305e75d37e20288e73414d43a0a711341"),
-    "rmat": (222.2, "R-MAT scale 18, 2000 trees, 64 walkers per tree: one w_trees launch "
+    "grid": (266.2, "grid 256x256, 2000 trees, 64 walkers per tree: one w_trees launch "
+                     "(565.0 GB over 2.123e9 draws)", "walker.cu",
+             "ab1fdc759f922dfae00450c5610e7341609c15fbdcdfceea4077a8a0d4278a2e"),
+    "rmat": (222.3, "R-MAT scale 18, 2000 trees, 64 walkers per tree: one w_trees launch "
                      "(171.0 GB over 7.693e8 draws)", "walker.cu",
-             "ec78c283b954dd69a2f710758762f74305e75d37e20288e73414d43a0a711341"),
+             "ab1fdc759f922dfae00450c5610e7341609c15fbdcdfceea4077a8a0d4278a2e"),
 }
 
 

@@ -113,8 +113,9 @@ __device__ __forceinline__ uint64_t gtimer() {
     return t;
 }
 
-// Walker states.  Each loop iteration ("tick") does at most one vertex of
-// work per walker, and the memory accesses of all states are issued by the
+// Walker states.  Each loop iteration ("tick") does one vertex of work per
+// walker (up to 8 on graphs with inline rows, below), and the memory
+// accesses of all states are issued by the
 // same instructions: one load of a vertex word (with the row of the vertex
 // that may be drawn), then the stores, the claim CAS and the successor draw,
 // whose arc load overlaps the CAS (on graphs of degree at most 8 the draw
@@ -189,6 +190,7 @@ __global__ void __maxnreg__(RWC_WALKER_MAXNREG) w_trees(DevGraph g, WState s, in
     __shared__ unsigned sh_prog;        // rewritten by every walker that stores a vertex word
     // claim locks of graphs with inline rows (below); all free between ticks
     constexpr int NLOCK = 256;
+    constexpr int KSTEP = EW > 0 ? 8 : 1;   // vertex steps per tick and lane (below)
     __shared__ int sh_lock[EW > 0 ? NLOCK : 1];
     if constexpr (EW > 0)
         for (int i = threadIdx.x; i < NLOCK; i += blockDim.x) sh_lock[i] = 0;
@@ -370,13 +372,22 @@ __global__ void __maxnreg__(RWC_WALKER_MAXNREG) w_trees(DevGraph g, WState s, in
             }
             if (hold) continue;
 
+            // a lane in WALK, POP, REL or SET goes on for up to KSTEP vertex
+            // steps in one tick while each step makes progress (a store, a
+            // held claim or a change of pass), so one tick's fixed cost (votes,
+            // the other lanes' states) is shared by several steps: 7% on a
+            // 1024² grid with 8; on R-MAT under load the longer divergent ticks
+            // cost more than they save (R-MAT 20: 9% slower with 2), so there
+            // a lane takes one step per tick
+            for (int ms = 0;; ++ms) {
+            const int st0 = state;
             // ---- the vertex word of this tick, and the row of a possible draw
             int32_t a = -1, dv = -1;
             if (state == S_WALK || state == S_WAITK || state == S_WAITH) a = head < 0 ? start : hp;
             else if (state == S_POP || state == S_REL || state == S_SET) a = cur;
             if (state == S_WALK) dv = a;
             else if (state == S_POP && cur == head) dv = popx;
-            if (a < 0) continue;
+            if (a < 0) break;
             const uint64_t w = ldv(st + a);
             DrawRow<OFF64, EW> row;
             if (dv >= 0) row.load(g, dv);
@@ -398,7 +409,7 @@ __global__ void __maxnreg__(RWC_WALKER_MAXNREG) w_trees(DevGraph g, WState s, in
                     state = S_WALK;
                     polls = 0;
                 }
-                continue;
+                break;
             }
             if (state == S_POP) {
                 // one vertex of the loop popx -> ... -> head (popx itself was
@@ -417,7 +428,7 @@ __global__ void __maxnreg__(RWC_WALKER_MAXNREG) w_trees(DevGraph g, WState s, in
                 if (state == S_REL && cut >= 0 && cur == cut && head != -2 && W_own(w) != me) {
                     // the requested vertex has left the path meanwhile
                     cut = -1; cur = start; walked = 0;
-                    continue;
+                    break;
                 }
                 if (W_own(w) != me || ++walked > n) { atomicOr(&sh_err, WERR_LOOP); break; }
                 s_v = cur; s_val = (w & ~OWN_MASK) | (state == S_REL ? OWN_FREE : OWN_SET);
@@ -538,6 +549,10 @@ __global__ void __maxnreg__(RWC_WALKER_MAXNREG) w_trees(DevGraph g, WState s, in
                 cut = -1;
                 drop_start(after == 3);
                 state = (after == 3 && wait_on >= 0 && must_wait()) ? S_WAITV : S_IDLE;
+            }
+            const bool go = (state == S_WALK || state == S_POP || state == S_REL || state == S_SET) &&
+                            !(c_v >= 0 && old != c_cmp) && (s_v >= 0 || c_v >= 0 || state != st0);
+            if (!go || ms + 1 >= KSTEP) break;
             }
             } while (0);
         }
