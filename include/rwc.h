@@ -23,7 +23,10 @@
  *    rwc_grad, rwc_batch_sample, rwc_trap_walks, rwc_auto_params,
  *    rwc_predict_mre) synchronise
  *    that stream before returning, so their outputs are ready on return and
- *    device-side errors come back as their status.
+ *    device-side errors come back as their status.  rwc_sample_trees with
+ *    rwc_options_t.async_status = 1 is the exception: it only enqueues, its
+ *    status covers argument and launch errors, and device-side errors are
+ *    recorded in the graph's status word and returned by rwc_sync_status.
  *  - Graphs are undirected, given as CSR with both arc directions: row u
  *    lists the neighbours of u.  Vertex ids are int32; n >= 2.
  *  - All functions are safe to call from several host threads on distinct
@@ -108,6 +111,12 @@ typedef struct {
                                  tree) has stored no vertex word for this many
                                  nanoseconds (0 = 30 s); the bound is on a lack of
                                  progress, not on the length of any one wait */
+    int32_t async_status;     /* 1 = return without synchronising the stream:
+                                 device-side errors go to the graph's status
+                                 word, read by rwc_sync_status.  WALKER (policies
+                                 0-3) and SHARED modes only, with stats = NULL
+                                 and profile = 0 (RWC_ERR_INVALID otherwise) */
+    int32_t reserved;
 } rwc_options_t;
 
 /* Sampler phases reported in rwc_stats_t.  GLOBAL mode: INIT, WALK, POP
@@ -209,6 +218,20 @@ rwc_status rwc_sample_trees(rwc_graph_t *g, uint64_t seed, int64_t tree0,
                             int64_t num_trees, double *sums, int32_t *parents,
                             int32_t *visits, const rwc_options_t *opt,
                             rwc_stats_t *stats, rwc_stream_t stream);
+
+/*
+ * Device-side status of the asynchronous calls on g (rwc_options_t.
+ * async_status = 1).  Synchronises stream, then reads and clears g's status
+ * word, which every asynchronous sampling call ORs its device-side errors
+ * into as its last step on its stream: RWC_ERR_UNSUPPORTED (a pop count
+ * overflowed), RWC_ERR_CUDA (an internal check failed), RWC_ERR_NOT_CONVERGED
+ * (a walker wait ran out, or max_rounds was reached in SHARED mode), in that
+ * order of precedence; the outputs of the failed call are undefined.  Errors
+ * of calls still running on other streams are reported by a later call once
+ * those streams are synchronised.  Not a counterpart of any step of the
+ * paper: it completes the asynchronous form of rwc_sample_trees.
+ */
+rwc_status rwc_sync_status(rwc_graph_t *g, rwc_stream_t stream);
 
 /*
  * rwc_sample_trees without any allocation (the paper has no counterpart).

@@ -35,12 +35,13 @@ class Options(ctypes.Structure):
                 ("trees_per_chunk", ctypes.c_int64), ("use_jumps", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("memory_budget", ctypes.c_int64),
                 ("profile", ctypes.c_int32), ("walker_policy", ctypes.c_int32),
-                ("max_wait_ns", ctypes.c_int64)]
+                ("max_wait_ns", ctypes.c_int64), ("async_status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
     def __init__(self, mode=0, max_rounds=0, trees_per_chunk=0, use_jumps=-1, block_threads=0,
-                 memory_budget=0, profile=0, walker_policy=0, max_wait_ns=0):
+                 memory_budget=0, profile=0, walker_policy=0, max_wait_ns=0, async_status=0):
         super().__init__(mode, max_rounds, trees_per_chunk, use_jumps, block_threads,
-                         memory_budget, profile, walker_policy, max_wait_ns)
+                         memory_budget, profile, walker_policy, max_wait_ns, async_status, 0)
 
 
 class Params(ctypes.Structure):
@@ -90,6 +91,7 @@ def lib():
         "rwc_graph_create": ([_i64, _i64, _vp, _vp, _vp, _i32, _u32, ctypes.POINTER(_vp)], _i32),
         "rwc_graph_info": ([_vp, ctypes.POINTER(GraphInfo)], _i32),
         "rwc_graph_destroy": ([_vp], _i32),
+        "rwc_sync_status": ([_vp, _vp], _i32),
         "rwc_sample_trees": ([_vp, _u64, _i64, _i64, _vp, _vp, _vp, ctypes.POINTER(Options),
                               ctypes.POINTER(Stats), _vp], _i32),
         "rwc_sample_trees_noalloc": ([_vp, _u64, _i64, _i64, _vp, _vp, _vp, _vp], _i32),
@@ -195,16 +197,25 @@ def rwc_graph_destroy(g):
 
 
 def rwc_sample_trees(g, seed, tree0, num_trees, sums, parents=None, visits=None, opt=None,
-                     stream=None) -> Stats:
+                     stream=None):
+    """Returns the call's Stats; None for an asynchronous call (opt.async_status
+    = 1), whose device-side errors rwc_sync_status reports."""
     import torch
-    st = Stats()
+    asy = opt is not None and opt.async_status != 0
+    st = None if asy else Stats()
     _check(lib().rwc_sample_trees(g, int(seed), int(tree0), int(num_trees),
                                   _dptr(sums, torch.float64, "sums"),
                                   _dptr(parents, torch.int32, "parents"),
                                   _dptr(visits, torch.int32, "visits"),
                                   ctypes.byref(opt) if opt is not None else None,
-                                  ctypes.byref(st), _stream(stream)))
+                                  ctypes.byref(st) if st is not None else None, _stream(stream)))
     return st
+
+
+def rwc_sync_status(g, stream=None):
+    """Synchronise the stream and raise the device-side error of the graph's
+    asynchronous sampling calls, if any (the status word is cleared)."""
+    _check(lib().rwc_sync_status(g, _stream(stream)))
 
 
 def rwc_sample_trees_noalloc(g, seed, tree0, num_trees, sums, parents=None, visits=None,

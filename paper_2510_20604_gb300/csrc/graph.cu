@@ -335,6 +335,12 @@ static rwc_status create_impl(int64_t n, int64_t nnz, const int64_t *rp, const i
             g.ell_w = ew;
         }
     }
+    {
+        int *ps;
+        if ((e = graph_alloc(G, (void **)&ps, 256)) != cudaSuccess) return fail(e, "status word");
+        if ((e = cudaMemset(ps, 0, 256)) != cudaSuccess) return fail(e, "status word");
+        G->dev_status = ps;
+    }
     if ((e = cudaMallocHost((void **)&G->host_scalars, 64 * sizeof(int64_t))) != cudaSuccess)
         return fail(e, "pinned scalars");
     *out = G;

@@ -88,6 +88,8 @@ struct rwc_graph {
     int64_t *host_scalars = nullptr;
     // start order of the walker sampler (device, n-1 entries), made on first use
     int32_t *walk_order = nullptr;
+    // device status word of asynchronous sampling calls (STATUS_* bits)
+    int *dev_status = nullptr;
 };
 
 namespace rwc {
@@ -172,6 +174,26 @@ __device__ __forceinline__ int32_t succ(const DevGraph &g, int32_t u, uint32_t c
     } else {
         return __ldg(g.col + b + j);
     }
+}
+
+// ------------------------------------------ asynchronous status word
+// Bits of rwc_graph::dev_status, set by asynchronous sampling calls and read
+// and cleared by rwc_sync_status.
+constexpr int STATUS_KOVF = 1;       // a pop count overflowed
+constexpr int STATUS_WAIT = 2;       // a walker wait ran out
+constexpr int STATUS_INTERNAL = 4;   // an internal consistency check failed
+constexpr int STATUS_ROUNDS = 8;     // max_rounds reached (shared mode)
+
+// dst |= the status bits of a sampler's error word: walker words use the
+// STATUS_* values already; shared-mode words (rounds 1, overflow 2, check 4)
+// are mapped.  One thread.  (static: every translation unit has its own copy.)
+static __global__ void fold_status(const int *err, int shared_codes, int *dst) {
+    const int e = *err;
+    if (!e) return;
+    int b = e;
+    if (shared_codes)
+        b = ((e & 1) ? STATUS_ROUNDS : 0) | ((e & 2) ? STATUS_KOVF : 0) | ((e & 4) ? STATUS_INTERNAL : 0);
+    atomicOr(dst, b);
 }
 
 // ------------------------------------------------------------- helpers

@@ -383,6 +383,13 @@ static rwc_status sample_shared(rwc_graph *G, uint64_t seed, int64_t tree0, int6
     });
     RWC_TRY(status);
     RWC_CUDA_TRY(cudaGetLastError());
+    if (o.async_status) {
+        // no host synchronisation: the error bits go to the graph's status word
+        ::rwc::count_launches(1);
+        fold_status<<<1, 1, 0, stream>>>(err, 1, G->dev_status);
+        RWC_CUDA_TRY(cudaGetLastError());
+        return RWC_OK;
+    }
     int64_t *h = G->host_scalars;
     RWC_CUDA_TRY(cudaMemcpyAsync(h, scr.p, 32, cudaMemcpyDeviceToHost, stream));
     RWC_CUDA_TRY(cudaStreamSynchronize(stream));
@@ -598,6 +605,14 @@ extern "C" rwc_status rwc_sample_trees(rwc_graph_t *G, uint64_t seed, int64_t tr
         mode = (g.n <= 20000 && shared_bytes(g.n) <= 200 * 1024) ? RWC_MODE_SHARED : RWC_MODE_WALKER;
     if (mode == RWC_MODE_SHARED && (g.n > 32767 || shared_bytes(g.n) > 227 * 1024))
         return set_error(RWC_ERR_UNSUPPORTED, "shared mode needs n <= 20000");
+    if (o.async_status) {
+        if (stats || o.profile)
+            return set_error(RWC_ERR_INVALID, "asynchronous sampling (async_status = 1) fills no "
+                                              "statistics: pass stats = NULL and profile = 0");
+        if (mode == RWC_MODE_GLOBAL || (mode == RWC_MODE_WALKER && o.walker_policy == 4))
+            return set_error(RWC_ERR_UNSUPPORTED, "asynchronous sampling needs WALKER mode (policies "
+                                                  "0-3) or SHARED mode");
+    }
     rwc_status s;
     try {
         if (mode == RWC_MODE_SHARED)
@@ -613,4 +628,20 @@ extern "C" rwc_status rwc_sample_trees(rwc_graph_t *G, uint64_t seed, int64_t tr
     }
     if (s == RWC_OK && stats) stats->trees = T;
     return s;
+}
+
+extern "C" rwc_status rwc_sync_status(rwc_graph_t *G, rwc_stream_t stream) {
+    using namespace rwc;
+    clear_error();
+    if (!G) return set_error(RWC_ERR_INVALID, "graph is NULL");
+    RWC_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    int e = 0;
+    RWC_CUDA_TRY(cudaMemcpy(&e, G->dev_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!e) return RWC_OK;
+    RWC_CUDA_TRY(cudaMemset(G->dev_status, 0, sizeof(int)));
+    if (e & STATUS_KOVF) return set_error(RWC_ERR_UNSUPPORTED, "a vertex was popped too many times "
+                                          "(2^20 - 1 in WALKER mode, 65535 in SHARED mode)");
+    if (e & STATUS_INTERNAL) return set_error(RWC_ERR_CUDA, "sampler internal check failed");
+    if (e & STATUS_WAIT) return set_error(RWC_ERR_NOT_CONVERGED, "a walker wait exceeded its bound");
+    return set_error(RWC_ERR_NOT_CONVERGED, "cycle popping exceeded max_rounds");
 }

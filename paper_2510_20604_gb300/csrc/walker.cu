@@ -733,6 +733,14 @@ rwc_status sample_walker(rwc_graph *G, uint64_t seed, int64_t tree0, int64_t T, 
                                              visits ? visits + c0 * n : nullptr, draws);
         if (prof) cudaEventRecord(ev[3], stream);
         RWC_CUDA_TRY(cudaGetLastError());
+        if (o.async_status) {
+            // no host synchronisation: the chunk's error bits go to the
+            // graph's status word (rwc_sync_status)
+            ::rwc::count_launches(1);
+            fold_status<<<1, 1, 0, stream>>>((const int *)tail, 0, G->dev_status);
+            RWC_CUDA_TRY(cudaGetLastError());
+            continue;
+        }
         RWC_CUDA_TRY(cudaMemcpyAsync(h, tail, 128, cudaMemcpyDeviceToHost, stream));
         RWC_CUDA_TRY(cudaStreamSynchronize(stream));
         const int e = (int)(h[0] & 0xffffffff);
