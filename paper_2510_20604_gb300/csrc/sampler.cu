@@ -503,14 +503,19 @@ static rwc_status sample_global(rwc_graph *G, uint64_t seed, int64_t tree0, int6
             cudaGraph_t gr = nullptr;
             RWC_CUDA_TRY(cudaStreamBeginCapture(guard.cs, cudaStreamCaptureModeThreadLocal));
             for (int q = 0; q < Q; ++q) {
-                if (prof) cudaEventRecord(ev[2 * q], guard.cs);
+                // events recorded inside the captured rounds must be external
+                // records (graph nodes that record them on replay) to be timed
+                if (prof) cudaEventRecordWithFlags(ev[2 * q], guard.cs, cudaEventRecordExternal);
                 g_walk<<<grid, 256, 0, guard.cs>>>(n, s, use_jumps);
-                if (prof) { cudaEventRecord(ev[2 * q + 1], guard.cs); cudaEventRecord(ev[2 * Q + 2 * q], guard.cs); }
+                if (prof) {
+                    cudaEventRecordWithFlags(ev[2 * q + 1], guard.cs, cudaEventRecordExternal);
+                    cudaEventRecordWithFlags(ev[2 * Q + 2 * q], guard.cs, cudaEventRecordExternal);
+                }
                 dispatch(g, [&](auto off64, auto wt) {
                     constexpr bool O = decltype(off64)::value, Wt = decltype(wt)::value;
                     g_pop<O, Wt><<<grid, 256, 0, guard.cs>>>(g, s, t0, k0, k1);
                 });
-                if (prof) cudaEventRecord(ev[2 * Q + 2 * q + 1], guard.cs);
+                if (prof) cudaEventRecordWithFlags(ev[2 * Q + 2 * q + 1], guard.cs, cudaEventRecordExternal);
             }
             const cudaError_t ce = cudaStreamEndCapture(guard.cs, &gr);
             if (ce != cudaSuccess) {

@@ -154,6 +154,20 @@ def test_explicit_root_and_empty_call():
     assert st.trees == 0 and float(s.abs().sum()) == 0.0
 
 
+@pytest.mark.parametrize("mode", [rwc.MODE_SHARED, rwc.MODE_GLOBAL, rwc.MODE_WALKER])
+def test_profiled_call_times_its_phases_and_keeps_the_trees(mode):
+    # profile = 1 times the kernels with CUDA events (in GLOBAL mode, inside
+    # the captured round graphs); the sums are those of the unprofiled call
+    g = synth.grid2d(40, 45)
+    G = rwc.Graph.from_synth(g)
+    ref, _, _, _ = G.sample(6, opt=rwc.Options(mode=mode))
+    s, st, _, _ = G.sample(6, opt=rwc.Options(mode=mode, profile=1))
+    assert torch.equal(s, ref)
+    assert st.phase_ms[1] > 0 and st.phase_launches[1] >= 1
+    if mode == rwc.MODE_GLOBAL:
+        assert st.phase_ms[3] > 0 and st.phase_launches[3] == st.phase_launches[1]
+
+
 def test_max_rounds_reports_not_converged():
     g = synth.grid2d(30, 30)
     G = rwc.Graph.from_synth(g)
