@@ -30,7 +30,9 @@
  *  - Graphs are undirected, given as CSR with both arc directions: row u
  *    lists the neighbours of u.  Vertex ids are int32; n >= 2.
  *  - All functions are safe to call from several host threads on distinct
- *    handles; a single handle must not be used concurrently.
+ *    handles; a single handle must not be used concurrently, except that
+ *    rwc_pivot_solve (which only reads the graph's arrays) may run on one
+ *    thread while the same handle samples on another.
  */
 #ifndef RWC_H
 #define RWC_H
@@ -284,6 +286,18 @@ rwc_status rwc_estimate(rwc_graph_t *g, const double *sums, int64_t num_trees,
                         rwc_stream_t stream);
 
 /*
+ * The pivot column of Algorithm 1 alone: the steps of rwc_estimate before the
+ * recovery (b, z = L^+ b, y), which depend on the graph only and not on the
+ * sampled trees, so that they can run while the trees are sampled (on
+ * another stream, or once for many estimates of the same graph).  y: FP64
+ * [n] device, the same bits as rwc_estimate's y_out for the same cg_tol;
+ * rwc_recover(g, sums, num_trees, y, H) then gives rwc_estimate's H.
+ * cg_tol <= 0 selects 1e-10.  Returns RWC_ERR_NOT_CONVERGED if the solver
+ * stalls.  Synchronises stream.
+ */
+rwc_status rwc_pivot_solve(rwc_graph_t *g, double cg_tol, double *y, rwc_stream_t stream);
+
+/*
  * Recovery step only (Algorithm 1, the recovery of H from t and y) for a given pivot column y
  * (FP64 [n] device): H from sums/num_trees and y as in rwc_estimate.
  */
@@ -311,7 +325,10 @@ rwc_status rwc_solve(rwc_graph_t *g, int32_t k, const double *B, double *X,
  * and tr(C L^+) estimated by tr(Z C^1/2 Q^T).  Q (k x n) is the
  * Johnson-Lindenstrauss sketch: Q_iu = +-1/sqrt(k), the sign the top bit of
  * Philox output o0 for counter (i, u, 0xFFFFFFFF, 0) and key sketch_seed;
- * k = 0 means Q = I (exact, k = n right-hand sides; small graphs only).
+ * k = 0 means Q = I (exact, k = n right-hand sides; small graphs only: the
+ * solve's kernels hold two doubles per right-hand side in shared memory, so
+ * on a GB300 (227 KB per block) n up to about 14,500, 7,200 when c has both
+ * signs; beyond that, or above n = 16384, RWC_ERR_UNSUPPORTED).
  * c: FP64 [n] device, any signs: the term sum_u c_u (L^+ b_e)_u^2 and
  * tr(C L^+) are linear in c, so negative entries get their own k sketch
  * columns with C^1/2 replaced by (max(-c, 0))^1/2 and enter with sign -

@@ -11,7 +11,7 @@ host buffers (graph CSR) as numpy arrays.
 """
 from ._binding import (RWCError, Options, Stats, GraphInfo, lib, lib_path,
                        rwc_version, rwc_launch_count, rwc_last_error, rwc_graph_create, rwc_graph_info,
-                       rwc_graph_destroy, rwc_sample_trees, rwc_sample_trees_noalloc, rwc_sync_status,
+                       rwc_graph_destroy, rwc_sample_trees, rwc_sample_trees_noalloc, rwc_sync_status, rwc_pivot_solve,
                        rwc_estimate, rwc_recover,
                        rwc_solve, rwc_grad, rwc_batch_create, rwc_batch_sample,
                        rwc_batch_roots, rwc_autotune, rwc_batch_get_schedule, rwc_batch_set_schedule, rwc_batch_destroy, rwc_mre, rwc_kendall, rwc_auto_params, Params, rwc_trap_walks, rwc_predict_mre,
@@ -23,7 +23,7 @@ __all__ = [
     "RWCError", "Options", "Stats", "GraphInfo", "lib", "lib_path", "rwc_version",
     "rwc_launch_count",
     "rwc_last_error", "rwc_graph_create", "rwc_graph_info", "rwc_graph_destroy",
-    "rwc_sample_trees", "rwc_sample_trees_noalloc", "rwc_sync_status", "rwc_estimate", "rwc_recover", "rwc_solve", "rwc_grad",
+    "rwc_sample_trees", "rwc_sample_trees_noalloc", "rwc_sync_status", "rwc_pivot_solve", "rwc_estimate", "rwc_recover", "rwc_solve", "rwc_grad",
     "rwc_batch_create", "rwc_batch_sample", "rwc_batch_roots", "rwc_autotune",
     "rwc_batch_get_schedule", "rwc_batch_set_schedule",
     "rwc_batch_destroy", "rwc_mre", "rwc_kendall", "rwc_auto_params", "Params", "rwc_trap_walks", "rwc_predict_mre", "MODE_AUTO", "MODE_GLOBAL", "MODE_SHARED", "MODE_WALKER",

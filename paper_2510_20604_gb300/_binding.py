@@ -92,6 +92,7 @@ def lib():
         "rwc_graph_info": ([_vp, ctypes.POINTER(GraphInfo)], _i32),
         "rwc_graph_destroy": ([_vp], _i32),
         "rwc_sync_status": ([_vp, _vp], _i32),
+        "rwc_pivot_solve": ([_vp, ctypes.c_double, _vp, _vp], _i32),
         "rwc_sample_trees": ([_vp, _u64, _i64, _i64, _vp, _vp, _vp, ctypes.POINTER(Options),
                               ctypes.POINTER(Stats), _vp], _i32),
         "rwc_sample_trees_noalloc": ([_vp, _u64, _i64, _i64, _vp, _vp, _vp, _vp], _i32),
@@ -234,6 +235,11 @@ def rwc_estimate(g, sums, num_trees, cg_tol, H_out, y_out=None, stream=None):
     _check(lib().rwc_estimate(g, _dptr(sums, torch.float64, "sums"), int(num_trees),
                               float(cg_tol), _dptr(H_out, torch.float64, "H_out"),
                               _dptr(y_out, torch.float64, "y_out"), _stream(stream)))
+
+
+def rwc_pivot_solve(g, cg_tol, y, stream=None):
+    import torch
+    _check(lib().rwc_pivot_solve(g, float(cg_tol), _dptr(y, torch.float64, "y"), _stream(stream)))
 
 
 def rwc_recover(g, sums, num_trees, y, H_out, stream=None):

@@ -228,6 +228,42 @@ extern "C" rwc_status rwc_recover(rwc_graph_t *G, const double *sums, int64_t T,
     return RWC_OK;
 }
 
+namespace rwc {
+namespace {
+// Algorithm 1's pivot column: b = sqrt(d_v) e_v - (sqrt(d_v) / vol) d,
+// z = L^+ b, y_u = sqrt(d_u) z_u - sqrt(d_u) (sum_w d_w z_w) / vol.  It
+// depends on the graph only, not on the sampled trees.  Enqueued on st; the
+// solver itself synchronises st between refinements.
+rwc_status pivot_column(rwc_graph *G, double tol, double *y, cudaStream_t st) {
+    const DevGraph &g = G->g;
+    const int64_t n = g.n;
+    Buf buf(st);
+    const unsigned gs = grid_for(n);
+    RWC_CUDA_TRY(cudaMallocAsync(&buf.p, (size_t)n * 2 * sizeof(double) + (size_t)(gs + 8) * sizeof(double), st));
+    double *b = (double *)buf.p, *z = b + n;
+    double *dz = (double *)((char *)buf.p + (size_t)n * 2 * sizeof(double));
+    double *parts = dz + 8;
+    ::rwc::count_launches(1); rhs_pivot<<<gs, TPB, 0, st>>>(n, g.d, g.root, g.vol, b);
+    RWC_CUDA_TRY(cudaGetLastError());
+    RWC_TRY(solve_nodemajor(G, 1, b, z, tol > 0 ? tol : 1e-10, nullptr, st));
+    ::rwc::count_launches(1); dot64<<<gs, TPB, 0, st>>>(n, g.d, z, parts);
+    ::rwc::count_launches(1); sum_parts<<<1, TPB, 0, st>>>(parts, (int)gs, 0, 1, dz);
+    ::rwc::count_launches(1); y_from_z<<<gs, TPB, 0, st>>>(n, g.d, z, dz, g.vol, y);
+    RWC_CUDA_TRY(cudaGetLastError());
+    return RWC_OK;
+}
+}  // namespace
+}  // namespace rwc
+
+extern "C" rwc_status rwc_pivot_solve(rwc_graph_t *G, double tol, double *y, rwc_stream_t stream) {
+    clear_error();
+    if (!G || !y) return set_error(RWC_ERR_INVALID, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    RWC_TRY(pivot_column(G, tol, y, st));
+    RWC_CUDA_TRY(cudaStreamSynchronize(st));
+    return RWC_OK;
+}
+
 extern "C" rwc_status rwc_estimate(rwc_graph_t *G, const double *sums, int64_t T, double tol,
                                    double *H, double *y_out, rwc_stream_t stream) {
     clear_error();
@@ -236,18 +272,13 @@ extern "C" rwc_status rwc_estimate(rwc_graph_t *G, const double *sums, int64_t T
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = g.n;
     Buf buf(st);
-    const unsigned gs = grid_for(n);
-    RWC_CUDA_TRY(cudaMallocAsync(&buf.p, (size_t)n * 3 * sizeof(double) + (size_t)(gs + 8) * sizeof(double), st));
-    double *b = (double *)buf.p, *z = b + n, *y = y_out ? y_out : z + n;
-    double *dz = (double *)((char *)buf.p + (size_t)n * 3 * sizeof(double));
-    double *parts = dz + 8;
-    ::rwc::count_launches(1); rhs_pivot<<<gs, TPB, 0, st>>>(n, g.d, g.root, g.vol, b);
-    RWC_CUDA_TRY(cudaGetLastError());
-    RWC_TRY(solve_nodemajor(G, 1, b, z, tol > 0 ? tol : 1e-10, nullptr, st));
-    ::rwc::count_launches(1); dot64<<<gs, TPB, 0, st>>>(n, g.d, z, parts);
-    ::rwc::count_launches(1); sum_parts<<<1, TPB, 0, st>>>(parts, (int)gs, 0, 1, dz);
-    ::rwc::count_launches(1); y_from_z<<<gs, TPB, 0, st>>>(n, g.d, z, dz, g.vol, y);
-    ::rwc::count_launches(1); recover<<<gs, TPB, 0, st>>>(n, g.d, g.root, g.vol, sums, 1.0 / (double)T, y, H);
+    double *y = y_out;
+    if (!y) {
+        RWC_CUDA_TRY(cudaMallocAsync(&buf.p, (size_t)n * sizeof(double), st));
+        y = (double *)buf.p;
+    }
+    RWC_TRY(pivot_column(G, tol, y, st));
+    ::rwc::count_launches(1); recover<<<grid_for(n), TPB, 0, st>>>(n, g.d, g.root, g.vol, sums, 1.0 / (double)T, y, H);
     RWC_CUDA_TRY(cudaGetLastError());
     RWC_CUDA_TRY(cudaStreamSynchronize(st));
     return RWC_OK;

@@ -149,3 +149,21 @@ def test_pivot_solve_is_bit_reproducible(gname):
     outs = [G.estimate(sums, 16, want_y=True) for _ in range(4)]
     for H, y in outs[1:]:
         assert torch.equal(H, outs[0][0]) and torch.equal(y, outs[0][1])
+
+
+@pytest.mark.parametrize("gname", ["grid", "weighted_rmat"])
+def test_pivot_solve_then_recover_equals_estimate(gname):
+    """rwc_pivot_solve computes the pivot column alone (it needs no trees, so it
+    can run beside the sampling, on another stream); with rwc_recover it gives
+    rwc_estimate's y and H bit for bit."""
+    g = {"grid": lambda: synth.grid2d(90, 70),
+         "weighted_rmat": lambda: synth.rmat(13, 16, seed=6, sigma=1.0)}[gname]()
+    G = rwc.Graph.from_synth(g)
+    sums, _, _, _ = G.sample(12, seed=5)
+    H_ref, y_ref = G.estimate(sums, 12, want_y=True)
+    y = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    side = torch.cuda.Stream()
+    rwc.rwc_pivot_solve(G.handle, 1e-10, y, stream=side.cuda_stream)
+    H = torch.empty_like(y)
+    rwc.rwc_recover(G.handle, sums, 12, y, H)
+    assert torch.equal(y, y_ref) and torch.equal(H, H_ref)
