@@ -654,6 +654,29 @@ rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, doub
     double *parts = it_sc + (sc_count - 8 * (size_t)k);   // [3][PMAX] fixed-order block parts
     float *hsum = (float *)(parts + 3 * (size_t)PMAX);   // [hc_n] heavy-chunk sums
     const size_t shk = (size_t)k * sizeof(double), shk2 = 2 * shk;
+    if (k > 1 && shk2 > 48 * 1024) {
+        // the k-column kernels keep k (inner_update 2k) per-column doubles in
+        // shared memory: above the default 48 KB they must opt in
+        int dev_ = 0, optin = 0;
+        cudaGetDevice(&dev_);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev_);
+        if (shk2 > (size_t)optin)
+            return set_error(RWC_ERR_UNSUPPORTED, "%d right-hand sides need %zu bytes of shared memory per "
+                             "block (the device allows %d)", k, shk2, optin);
+        RWC_CUDA_TRY(cudaFuncSetAttribute(center64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shk));
+        RWC_CUDA_TRY(cudaFuncSetAttribute(colsum64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shk));
+        RWC_CUDA_TRY(cudaFuncSetAttribute(inner_start, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shk));
+        RWC_CUDA_TRY(cudaFuncSetAttribute(inner_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shk2));
+        cudaError_t ae = cudaSuccess;
+        dispatch(g, [&](auto o64, auto wt) {
+            constexpr bool O = decltype(o64)::value, Wt = decltype(wt)::value;
+            if (ae == cudaSuccess)
+                ae = cudaFuncSetAttribute(spmm32<O, Wt>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shk);
+            if (ae == cudaSuccess)
+                ae = cudaFuncSetAttribute(resid64<O, Wt>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shk);
+        });
+        RWC_CUDA_TRY(ae);
+    }
     const unsigned gs = grid_for(nk), gw = grid_for(n * 32);
     const int vw = pick_vw(g);
     const unsigned gv = grid_for(n * vw);

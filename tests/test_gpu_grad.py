@@ -127,3 +127,14 @@ def test_exact_gradient_on_parallel_arcs():
     _assert_per_edge(gg, ref, 1e-3)
     same = (np.diff(a) == 0) & (np.diff(b) == 0)
     assert same.any() and np.allclose(gg[1:][same], gg[:-1][same], rtol=1e-6, atol=0)
+
+
+def test_exact_gradient_with_more_right_hand_sides_than_default_shared_memory():
+    # n + 2 = 3302 right-hand sides: the solve's per-column shared memory
+    # (2 x 3302 doubles) is above the default 48 KB and must be opted into
+    g = synth.rgg(3300, 10.0, seed=5, sigma=0.5)
+    G = rwc.Graph.from_synth(g)
+    c = synth.uniform_vector(g.n, 21)
+    gg = G.grad(torch.tensor(c, dtype=torch.float64, device="cuda"), k=0, tol=1e-10).double().cpu().numpy()
+    a, b, w = _edges(g)
+    _assert_per_edge(gg, og.grad_closed(g.n, a, b, w, c), 1e-3)
