@@ -325,10 +325,9 @@ rwc_status rwc_solve(rwc_graph_t *g, int32_t k, const double *B, double *X,
  * and tr(C L^+) estimated by tr(Z C^1/2 Q^T).  Q (k x n) is the
  * Johnson-Lindenstrauss sketch: Q_iu = +-1/sqrt(k), the sign the top bit of
  * Philox output o0 for counter (i, u, 0xFFFFFFFF, 0) and key sketch_seed;
- * k = 0 means Q = I (exact, k = n right-hand sides; small graphs only: the
- * solve's kernels hold two doubles per right-hand side in shared memory, so
- * on a GB300 (227 KB per block) n up to about 14,500, 7,200 when c has both
- * signs; beyond that, or above n = 16384, RWC_ERR_UNSUPPORTED).
+ * k = 0 means Q = I (exact, k = n right-hand sides; n <= 16384, else
+ * RWC_ERR_UNSUPPORTED).  Every sum of the solve and of the assembly is taken
+ * in a fixed order, so the same input gives the same bits on every call.
  * c: FP64 [n] device, any signs: the term sum_u c_u (L^+ b_e)_u^2 and
  * tr(C L^+) are linear in c, so negative entries get their own k sketch
  * columns with C^1/2 replaced by (max(-c, 0))^1/2 and enter with sign -

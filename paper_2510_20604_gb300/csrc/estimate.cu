@@ -128,8 +128,9 @@ __global__ void any_negative(int64_t n, const double *c, int *flag) {
 }
 
 // tr(C L^+) estimate tr(Z C^1/2 Q^T) = sum_u sum_i X[u][i] R[u][i] over the
-// sketch columns, the second part (c-) with sign -.
-__global__ void grad_trace(int64_t n, int K, int NP, const double *X, const double *R, double *out) {
+// sketch columns, the second part (c-) with sign -.  Block parts in parts
+// (added in block order by sum_parts).
+__global__ void grad_trace(int64_t n, int K, int NP, const double *X, const double *R, double *parts) {
     const int64_t KS = (int64_t)NP * K, cols = KS + 2, tot = n * cols;
     double s = 0.0;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
@@ -138,19 +139,19 @@ __global__ void grad_trace(int64_t n, int K, int NP, const double *X, const doub
         if (j < K) s += X[idx] * R[idx];
         else if (j < KS) s -= X[idx] * R[idx];
     }
-    s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(out, s);
+    s = block_sum_fixed(s);
+    if (threadIdx.x == 0) parts[blockIdx.x] = s;
 }
 
-// out += sum_u X[u][col] * w[u]
+// sum_u X[u][col] * w[u]: block parts in parts (added by sum_parts).
 __global__ void col_dot(int64_t n, int64_t cols, int64_t col, const double *X, const double *w,
-                        double *out) {
+                        double *parts) {
     double s = 0.0;
     for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
          u += (int64_t)gridDim.x * blockDim.x)
         s += X[u * cols + col] * w[u];
-    s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(out, s);
+    s = block_sum_fixed(s);
+    if (threadIdx.x == 0) parts[blockIdx.x] = s;
 }
 
 // Number of arcs (a, b) with b > a in each row (rows sorted ascending).
@@ -332,23 +333,32 @@ extern "C" rwc_status rwc_grad(rwc_graph_t *G, const double *c, int32_t k, uint6
     }
     const int64_t cols = (int64_t)NP * K + 2;
     Buf buf(st);
-    const size_t bytes = (size_t)n * cols * 2 * sizeof(double) + (size_t)n * (8 + 4 + 4) + 256;
+    const size_t pcap = (size_t)num_sms() * 8;   // grid_for's largest grid: block parts below
+    const size_t bytes = (size_t)n * cols * 2 * sizeof(double) + (size_t)n * (8 + 4 + 4) + 256 +
+                         pcap * sizeof(double);
     RWC_CUDA_TRY(cudaMallocAsync(&buf.p, bytes, st));
     double *R = (double *)buf.p, *X = R + (size_t)n * cols;
     int64_t *off = (int64_t *)(X + (size_t)n * cols);
     int32_t *cnt = (int32_t *)(off + n), *first = cnt + n;
-    double *scal = (double *)(((uintptr_t)(first + n) + 63) & ~(uintptr_t)63);
+    double *scal = (double *)(((uintptr_t)(first + n) + 63) & ~(uintptr_t)63);   // [8]
+    double *tparts = scal + 8;                                                      // [pcap]
     ::rwc::count_launches(1); grad_rhs<<<grid_for(n * cols), TPB, 0, st>>>(n, K, NP, exact, c, g.d, (uint32_t)seed,
                                                  (uint32_t)(seed >> 32), R);
     RWC_CUDA_TRY(cudaGetLastError());
     RWC_TRY(solve_nodemajor(G, (int)cols, R, X, tol > 0 ? tol : 1e-8, nullptr, st));
     RWC_CUDA_TRY(cudaMemsetAsync(scal, 0, 4 * sizeof(double), st));
-    ::rwc::count_launches(1); grad_trace<<<grid_for(n * cols), TPB, 0, st>>>(n, K, NP, X, R, scal);
-    ::rwc::count_launches(1); col_dot<<<grid_for(n), TPB, 0, st>>>(n, cols, cols - 1, X, g.d, scal + 1);   // d^T y
-    {   // sum c, in a fixed order (the parts reuse the offsets buffer before it is filled)
-        double *cparts = (double *)off;
-        ::rwc::count_launches(1); dot64<<<grid_for(n), TPB, 0, st>>>(n, c, nullptr, cparts);
-        ::rwc::count_launches(1); sum_parts<<<1, TPB, 0, st>>>(cparts, (int)grid_for(n), 0, 1, scal + 2);
+    {   // tr(C L^+), d^T y and sum c, each in a fixed order (block parts added in
+        // block order)
+        const unsigned gt = grid_for(n * cols), gn = grid_for(n);
+        ::rwc::count_launches(2);
+        grad_trace<<<gt, TPB, 0, st>>>(n, K, NP, X, R, tparts);
+        sum_parts<<<1, TPB, 0, st>>>(tparts, (int)gt, 0, 1, scal);
+        ::rwc::count_launches(2);
+        col_dot<<<gn, TPB, 0, st>>>(n, cols, cols - 1, X, g.d, tparts);   // d^T y
+        sum_parts<<<1, TPB, 0, st>>>(tparts, (int)gn, 0, 1, scal + 1);
+        ::rwc::count_launches(2);
+        dot64<<<gn, TPB, 0, st>>>(n, c, nullptr, tparts);
+        sum_parts<<<1, TPB, 0, st>>>(tparts, (int)gn, 0, 1, scal + 2);
     }
     dispatch_off(g, [&](auto o64) {
         ::rwc::count_launches(1); upper_counts<decltype(o64)::value><<<grid_for(n), TPB, 0, st>>>(g, cnt, first);

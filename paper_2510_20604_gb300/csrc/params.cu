@@ -95,13 +95,20 @@ __global__ void farthest_min_id(int64_t n, const int32_t *dist, int *out) {
         if (dist[u] == ecc) atomicMin(out + 1, (int)u);
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+// Sums of the inverse iteration in a fixed order: each kernel stores its
+// block sums (block_sum_fixed) as parts[b] and, for a second sum,
+// parts[stride + b]; sum_parts adds them in block order.
+__device__ __forceinline__ void store_parts(double s0, double s1, int nv, double *parts, int stride) {
+    s0 = block_sum_fixed(s0);
+    if (threadIdx.x == 0) parts[blockIdx.x] = s0;
+    if (nv > 1) {
+        s1 = block_sum_fixed(s1);
+        if (threadIdx.x == 0) parts[stride + blockIdx.x] = s1;
+    }
 }
 
-// x_u = sqrt(d_u) for u != v, 0 at v; acc[0] += |x|^2, acc[1] += |d_-v|^2.
-__global__ void ii_start(int64_t n, const double *d, int32_t v, double *x, double *acc) {
+// x_u = sqrt(d_u) for u != v, 0 at v; sums |x|^2 and |d_-v|^2.
+__global__ void ii_start(int64_t n, const double *d, int32_t v, double *x, double *parts, int stride) {
     double s0 = 0.0, s1 = 0.0;
     for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
          u += (int64_t)gridDim.x * blockDim.x) {
@@ -110,13 +117,12 @@ __global__ void ii_start(int64_t n, const double *d, int32_t v, double *x, doubl
         s0 += xv * xv;
         if (u != v) s1 += d[u] * d[u];
     }
-    s0 = warp_sum(s0); s1 = warp_sum(s1);
-    if ((threadIdx.x & 31) == 0) { atomicAdd(acc, s0); atomicAdd(acc + 1, s1); }
+    store_parts(s0, s1, 2, parts, stride);
 }
 
-// c~ = D^1/2 x / |x| (0 at v); acc[0] += sum c.
+// c~ = D^1/2 x / |x| (0 at v); sum c.
 __global__ void ii_rhs(int64_t n, const double *d, int32_t v, const double *x, const double *xn2,
-                       double *c, double *acc) {
+                       double *c, double *parts, int stride) {
     const double inv = 1.0 / sqrt(*xn2);
     double s = 0.0;
     for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
@@ -125,16 +131,15 @@ __global__ void ii_rhs(int64_t n, const double *d, int32_t v, const double *x, c
         c[u] = cv;
         s += cv;
     }
-    s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0) atomicAdd(acc, s);
+    store_parts(s, 0.0, 1, parts, stride);
 }
 
 __global__ void ii_ground(int32_t v, double *c, const double *sum) { c[v] -= *sum; }
 
-// y = D^1/2 (z - z_v) (0 at v) written over x after <x/|x|, y> and |y|^2 are
-// accumulated: acc[0] += <x, y> / |x|, acc[1] += |y|^2.
+// y = D^1/2 (z - z_v) (0 at v) written over x after the sums <x, y> / |x|
+// and |y|^2.
 __global__ void ii_step(int64_t n, const double *d, int32_t v, const double *z, const double *xn2,
-                        double *x, double *acc) {
+                        double *x, double *parts, int stride) {
     const double zv = z[v], inv = 1.0 / sqrt(*xn2);
     double s0 = 0.0, s1 = 0.0;
     for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
@@ -144,8 +149,7 @@ __global__ void ii_step(int64_t n, const double *d, int32_t v, const double *z, 
         s1 += yv * yv;
         x[u] = yv;
     }
-    s0 = warp_sum(s0); s1 = warp_sum(s1);
-    if ((threadIdx.x & 31) == 0) { atomicAdd(acc, s0); atomicAdd(acc + 1, s1); }
+    store_parts(s0, s1, 2, parts, stride);
 }
 
 unsigned grid_n(int64_t n) {
@@ -188,13 +192,15 @@ extern "C" rwc_status rwc_auto_params(rwc_graph_t *G, double eps, int32_t max_it
     Buf buf(st);
     // dist [n] int32 | x, c, z [n] FP64 | scratch (flags, ints, sums)
     const size_t dist_b = (((size_t)n * 4) + 255) & ~(size_t)255;
-    RWC_CUDA_TRY(cudaMallocAsync(&buf.p, dist_b + 3 * (size_t)n * 8 + 256, st));
+    const int pstride = num_sms() * 8;    // grid_n's largest grid
+    RWC_CUDA_TRY(cudaMallocAsync(&buf.p, dist_b + 3 * (size_t)n * 8 + 256 + 2 * (size_t)pstride * 8, st));
     int32_t *dist = (int32_t *)buf.p;
     double *x = (double *)((char *)buf.p + dist_b), *c = x + n, *z = c + n;
     char *sc = (char *)(z + n);
     int *flag = (int *)sc;            // [3]
     int *iout = (int *)(sc + 16);     // [0] eccentricity, [1] farthest vertex
     double *acc = (double *)(sc + 64);
+    double *parts = (double *)(sc + 256);   // [2][pstride] block parts
     int64_t *h = G->host_scalars;
     const unsigned gs = grid_n(n);
 
@@ -219,8 +225,9 @@ extern "C" rwc_status rwc_auto_params(rwc_graph_t *G, double eps, int32_t max_it
     // ---- lambda by inverse iteration on the normalised grounded Laplacian
     const int32_t v = g.root;
     RWC_CUDA_TRY(cudaMemsetAsync(acc, 0, 4 * sizeof(double), st));
-    count_launches(1);
-    ii_start<<<gs, PT, 0, st>>>(n, g.d, v, x, acc);      // acc[0] = |x|^2, acc[1] = |d_-v|^2
+    count_launches(2);
+    ii_start<<<gs, PT, 0, st>>>(n, g.d, v, x, parts, pstride);
+    sum_parts<<<1, PT, 0, st>>>(parts, (int)gs, pstride, 2, acc);   // acc[0] = |x|^2, acc[1] = |d_-v|^2
     RWC_CUDA_TRY(cudaGetLastError());
     double hv[2];
     RWC_CUDA_TRY(cudaMemcpyAsync(hv, acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -232,14 +239,16 @@ extern "C" rwc_status rwc_auto_params(rwc_graph_t *G, double eps, int32_t max_it
     int it = 0;
     for (; it < max_iters; ++it) {
         RWC_CUDA_TRY(cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
-        count_launches(2);
-        ii_rhs<<<gs, PT, 0, st>>>(n, g.d, v, x, xn2, c, acc);
+        count_launches(3);
+        ii_rhs<<<gs, PT, 0, st>>>(n, g.d, v, x, xn2, c, parts, pstride);
+        sum_parts<<<1, PT, 0, st>>>(parts, (int)gs, pstride, 1, acc);
         ii_ground<<<1, 1, 0, st>>>(v, c, acc);
         RWC_CUDA_TRY(cudaGetLastError());
         RWC_TRY(solve_nodemajor(G, 1, c, z, 1e-11, nullptr, st));
         RWC_CUDA_TRY(cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
-        count_launches(1);
-        ii_step<<<gs, PT, 0, st>>>(n, g.d, v, z, xn2, x, acc);
+        count_launches(2);
+        ii_step<<<gs, PT, 0, st>>>(n, g.d, v, z, xn2, x, parts, pstride);
+        sum_parts<<<1, PT, 0, st>>>(parts, (int)gs, pstride, 2, acc);
         RWC_CUDA_TRY(cudaGetLastError());
         RWC_CUDA_TRY(cudaMemcpyAsync(xn2, acc + 1, sizeof(double), cudaMemcpyDeviceToDevice, st));
         RWC_CUDA_TRY(cudaMemcpyAsync(hv, acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));

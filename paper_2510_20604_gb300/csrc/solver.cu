@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include <cooperative_groups.h>
@@ -47,14 +48,12 @@ __device__ __forceinline__ float warp_sumf(float v) {
     return v;
 }
 
-// Q = L P (FP32), node-major [n][k], one warp per row; also accumulates the
-// per-column dots pq[c] += sum_u P[u][c] Q[u][c] (FP64).
+// Q = L P (FP32), node-major [n][k], k > 1, one warp per row, lanes over
+// columns.  (The per-column dots <P, Q> are taken by col_parts in a fixed
+// order.)
 template <bool OFF64, bool W>
 __global__ void __launch_bounds__(TPB) spmm32(DevGraph g, int k, const float *__restrict__ P,
-                                              float *__restrict__ Q, double *pq) {
-    extern __shared__ double sdot[];
-    for (int c = threadIdx.x; c < k; c += blockDim.x) sdot[c] = 0.0;
-    __syncthreads();
+                                              float *__restrict__ Q) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -62,40 +61,17 @@ __global__ void __launch_bounds__(TPB) spmm32(DevGraph g, int k, const float *__
         int64_t b, e;
         rowb<OFF64>(g, u, b, e);
         const float du = (float)g.d[u];
-        if (k == 1) {
+        for (int c0 = 0; c0 < k; c0 += 32) {
+            const int c = c0 + lane;
+            if (c >= k) continue;
             float s = 0.f;
-            for (int64_t j = b + lane; j < e; j += 32) {
+            for (int64_t j = b; j < e; ++j) {
                 const float wj = W ? g.w[j] : 1.f;
-                s += wj * P[g.col[j]];
+                s += wj * P[(int64_t)g.col[j] * k + c];
             }
-            s = warp_sumf(s);
-            if (lane == 0) {
-                const float pu = P[u];
-                const float q = du * pu - s;
-                Q[u] = q;
-                atomicAdd(&sdot[0], (double)pu * (double)q);
-            }
-        } else {
-            for (int c0 = 0; c0 < k; c0 += 32) {
-                const int c = c0 + lane;
-                float s = 0.f;
-                if (c < k)
-                    for (int64_t j = b; j < e; ++j) {
-                        const float wj = W ? g.w[j] : 1.f;
-                        s += wj * P[(int64_t)g.col[j] * k + c];
-                    }
-                if (c < k) {
-                    const float pu = P[u * k + c];
-                    const float q = du * pu - s;
-                    Q[u * k + c] = q;
-                    atomicAdd(&sdot[c], (double)pu * (double)q);
-                }
-            }
+            Q[u * k + c] = du * P[u * k + c] - s;
         }
     }
-    __syncthreads();
-    for (int c = threadIdx.x; c < k; c += blockDim.x)
-        if (sdot[c] != 0.0) atomicAdd(&pq[c], sdot[c]);
 }
 
 // k == 1 SpMV with VW lanes per row (VW = power of two <= 32 chosen from the
@@ -158,14 +134,10 @@ __global__ void __launch_bounds__(TPB) resid1(DevGraph g, const double *__restri
     if (threadIdx.x == 0) parts[blockIdx.x] = acc;
 }
 
-// R = B - L X in FP64 (node-major), and the column sums of R.
+// R = B - L X in FP64 (node-major), k > 1, one warp per row.
 template <bool OFF64, bool W>
 __global__ void __launch_bounds__(TPB) resid64(DevGraph g, int k, const double *__restrict__ B,
-                                               const double *__restrict__ X, double *__restrict__ R,
-                                               double *colsum) {
-    extern __shared__ double ssum[];
-    for (int c = threadIdx.x; c < k; c += blockDim.x) ssum[c] = 0.0;
-    __syncthreads();
+                                               const double *__restrict__ X, double *__restrict__ R) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -173,94 +145,82 @@ __global__ void __launch_bounds__(TPB) resid64(DevGraph g, int k, const double *
         int64_t b, e;
         rowb<OFF64>(g, u, b, e);
         const double du = g.d[u];
-        if (k == 1) {
+        for (int c0 = 0; c0 < k; c0 += 32) {
+            const int c = c0 + lane;
+            if (c >= k) continue;
             double s = 0.0;
-            for (int64_t j = b + lane; j < e; j += 32) {
+            for (int64_t j = b; j < e; ++j) {
                 const double wj = W ? (double)g.w[j] : 1.0;
-                s += wj * X[g.col[j]];
+                s += wj * X[(int64_t)g.col[j] * k + c];
             }
-            s = warp_sum(s);
-            if (lane == 0) {
-                const double r = B[u] - (du * X[u] - s);
-                R[u] = r;
-                atomicAdd(&ssum[0], r);
-            }
-        } else {
-            for (int c0 = 0; c0 < k; c0 += 32) {
-                const int c = c0 + lane;
-                if (c >= k) continue;
-                double s = 0.0;
-                for (int64_t j = b; j < e; ++j) {
-                    const double wj = W ? (double)g.w[j] : 1.0;
-                    s += wj * X[(int64_t)g.col[j] * k + c];
-                }
-                const double r = B[u * k + c] - (du * X[u * k + c] - s);
-                R[u * k + c] = r;
-                atomicAdd(&ssum[c], r);
-            }
+            R[u * k + c] = B[u * k + c] - (du * X[u * k + c] - s);
         }
     }
-    __syncthreads();
-    for (int c = threadIdx.x; c < k; c += blockDim.x)
-        if (ssum[c] != 0.0) atomicAdd(&colsum[c], ssum[c]);
 }
 
-// Per-column accumulation into shared memory: k == 1 sums in a register and
-// reduces once per warp; k > 1 adds element-wise (lanes hit distinct columns).
-struct ColAcc {
-    double *sh;
-    int k;
-    double reg = 0.0;
-    __device__ ColAcc(double *s, int kk) : sh(s), k(kk) {}
-    __device__ __forceinline__ void add(int c, double v) {
-        if (k == 1) reg += v;
-        else atomicAdd(&sh[c], v);
-    }
-    __device__ __forceinline__ void flush() {
-        if (k == 1) {
-            const double t = warp_sum(reg);
-            if ((threadIdx.x & 31) == 0 && t != 0.0) atomicAdd(&sh[0], t);
+// Per-column sums over the rows of a node-major [n][k] array, in a fixed
+// order (k > 1): block b adds the rows [b rpb, (b + 1) rpb), rpb =
+// ceil(n / gridDim).  With k < blockDim, thread t takes column t % k of the
+// rows t / k, t / k + P, ... (P = blockDim / k phases; consecutive threads read
+// consecutive words) and the phases' sums are added in phase order; otherwise
+// thread t takes the columns t, t + blockDim, ... over all the block's rows.
+// parts[c * gridDim + b] (and parts2 for COL_DOT2); sum_cols adds them in
+// block order, so a call of the same size gives the same bits every time.
+enum : int { COL_SUM = 0, COL_SQ = 1, COL_DOT = 2, COL_DOT2 = 3 };
+template <int OP, class T>
+__device__ __forceinline__ void col_term(const T *A, const T *Bv, int64_t i, double &a1, double &a2) {
+    const double x = (double)A[i];
+    if (OP == COL_SUM) a1 += x;
+    else if (OP == COL_SQ) a1 += x * x;
+    else if (OP == COL_DOT) a1 += x * (double)Bv[i];
+    else { a1 += x * (double)Bv[i]; a2 += x * x; }
+}
+template <int OP, class T>
+__global__ void __launch_bounds__(TPB) col_parts(int64_t n, int k, const T *__restrict__ A,
+                                                 const T *__restrict__ Bv, double *parts, double *parts2) {
+    __shared__ double s1[TPB], s2[TPB];
+    const int nb = gridDim.x, bk = blockIdx.x, t = threadIdx.x;
+    const int64_t rpb = (n + nb - 1) / nb;
+    const int64_t u0 = bk * rpb, u1 = u0 + rpb < n ? u0 + rpb : n;
+    if (k < (int)blockDim.x) {
+        const int P = (int)blockDim.x / k, c = t % k, ph = t / k;
+        double a1 = 0.0, a2 = 0.0;
+        if (ph < P)
+            for (int64_t u = u0 + ph; u < u1; u += P) col_term<OP>(A, Bv, u * k + c, a1, a2);
+        s1[t] = a1;
+        s2[t] = a2;
+        __syncthreads();
+        if (t < k) {
+            double r1 = 0.0, r2 = 0.0;
+            for (int q = 0; q < P; ++q) { r1 += s1[q * k + t]; r2 += s2[q * k + t]; }
+            parts[(int64_t)t * nb + bk] = r1;
+            if (OP == COL_DOT2) parts2[(int64_t)t * nb + bk] = r2;
+        }
+    } else {
+        for (int c = t; c < k; c += blockDim.x) {
+            double a1 = 0.0, a2 = 0.0;
+            for (int64_t u = u0; u < u1; ++u) col_term<OP>(A, Bv, u * k + c, a1, a2);
+            parts[(int64_t)c * nb + bk] = a1;
+            if (OP == COL_DOT2) parts2[(int64_t)c * nb + bk] = a2;
         }
     }
-};
-
-__device__ __forceinline__ void sh_zero(double *s, int k) {
-    for (int c = threadIdx.x; c < k; c += blockDim.x) s[c] = 0.0;
-    __syncthreads();
-}
-__device__ __forceinline__ void sh_flush(const double *s, int k, double *dst) {
-    __syncthreads();
-    for (int c = threadIdx.x; c < k; c += blockDim.x)
-        if (s[c] != 0.0) atomicAdd(&dst[c], s[c]);
 }
 
-// V[u][c] -= mean_c (FP64) and nrm[c] += V^2.
-__global__ void center64(int64_t n, int k, double *V, const double *colsum, double *nrm) {
-    extern __shared__ double sn[];
-    sh_zero(sn, k);
-    ColAcc acc(sn, k);
-    const int64_t tot = n * k;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % k);
-        const double v = V[i] - colsum[c] / (double)n;
-        V[i] = v;
-        acc.add(c, v * v);
-    }
-    acc.flush();
-    sh_flush(sn, k, nrm);
+// out[c] = sum over b of parts[c * nb + b] in order of b; one block per column.
+__global__ void __launch_bounds__(TPB) sum_cols(const double *parts, int nb, double *out) {
+    const int c = blockIdx.x;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += parts[(int64_t)c * nb + b];
+    s = block_sum_fixed(s);
+    if (threadIdx.x == 0) out[c] = s;
 }
 
-__global__ void colsum64(int64_t n, int k, const double *V, double *colsum) {
-    extern __shared__ double sn[];
-    sh_zero(sn, k);
-    ColAcc acc(sn, k);
+// V[u][c] -= colsum[c] / n (FP64), k > 1.
+__global__ void center64(int64_t n, int k, double *V, const double *colsum) {
     const int64_t tot = n * k;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
          i += (int64_t)gridDim.x * blockDim.x)
-        acc.add((int)(i % k), V[i]);
-    acc.flush();
-    sh_flush(sn, k, colsum);
+        V[i] -= colsum[(int)(i % k)] / (double)n;
 }
 
 // Single right-hand side versions with fixed-order block parts (the pivot
@@ -328,14 +288,10 @@ __global__ void inner_update1(int64_t n, const double *rz, const double *pq, con
     if (threadIdx.x == 0) { parts[blockIdx.x] = a1; parts[stride + blockIdx.x] = a2; }
 }
 
-// Start of an inner solve: r = R / |R_c| (FP32), e = 0, z = D^-1 r, p = z,
-// rz0[c] = <r, z>.
+// Start of an inner solve (k > 1): r = R / |R_c| (FP32), e = 0, z = D^-1 r,
+// p = z.  (rz0[c] = <r, z> by col_parts.)
 __global__ void inner_start(int64_t n, int k, const double *R, const double *rnrm2,
-                            const float *dinv, float *r, float *e, float *z, float *p,
-                            double *rz0) {
-    extern __shared__ double s[];
-    sh_zero(s, k);
-    ColAcc acc(s, k);
+                            const float *dinv, float *r, float *e, float *z, float *p) {
     const int64_t tot = n * k;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -345,21 +301,14 @@ __global__ void inner_start(int64_t n, int k, const double *R, const double *rnr
         const float rv = nr > 0 ? (float)(R[i] / nr) : 0.f;
         const float zv = dinv[u] * rv;
         r[i] = rv; e[i] = 0.f; z[i] = zv; p[i] = zv;
-        acc.add(c, (double)rv * (double)zv);
     }
-    acc.flush();
-    sh_flush(s, k, rz0);
 }
 
-// alpha_c = rz[c] / pq[c]; e += alpha p; r -= alpha q; z = D^-1 r;
-// rz1[c] += <r, z>; rr1[c] += <r, r>.
+// k > 1: alpha_c = rz[c] / pq[c]; e += alpha p; r -= alpha q; z = D^-1 r.
+// (<r, z> and <r, r> by col_parts.)
 __global__ void inner_update(int64_t n, int k, const double *rz, const double *pq,
                              const float *dinv, const float *p, const float *q, float *e,
-                             float *r, float *z, double *rz1, double *rr1) {
-    extern __shared__ double s[];
-    double *s1 = s, *s2 = s + k;
-    sh_zero(s, 2 * k);
-    ColAcc a1(s1, k), a2(s2, k);
+                             float *r, float *z) {
     const int64_t tot = n * k;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -370,17 +319,7 @@ __global__ void inner_update(int64_t n, int k, const double *rz, const double *p
         e[i] += a * p[i];
         const float rv = r[i] - a * q[i];
         r[i] = rv;
-        const float zv = dinv[u] * rv;
-        z[i] = zv;
-        a1.add(c, (double)rv * (double)zv);
-        a2.add(c, (double)rv * (double)rv);
-    }
-    a1.flush();
-    a2.flush();
-    __syncthreads();
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
-        if (s1[c] != 0.0) atomicAdd(&rz1[c], s1[c]);
-        if (s2[c] != 0.0) atomicAdd(&rr1[c], s2[c]);
+        z[i] = dinv[u] * rv;
     }
 }
 
@@ -638,8 +577,12 @@ rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, doub
     const size_t sc_count = (size_t)(max_inner + 4) * sc_per_it + 8 * (size_t)k;
     const size_t hbytes = (size_t)(g.hc_n + 1) * sizeof(float);
     constexpr int PMAX = 4096;                             // block parts of one reduction
+    // k > 1: blocks of the column reductions and their [k][nbc] parts (two sets)
+    const unsigned nbc = k > 1 ? (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms() * 4,
+                                                                                  (n + 63) / 64)) : 0u;
+    const size_t cbytes = k > 1 ? 2 * (size_t)k * nbc * sizeof(double) : 0;
     const size_t bytes = (size_t)nk * sizeof(double) + 5 * fbytes + sc_count * sizeof(double) + hbytes +
-                         3 * PMAX * sizeof(double) + 1024;
+                         3 * PMAX * sizeof(double) + cbytes + 1024;
     RWC_CUDA_TRY(cudaMallocAsync(&buf.p, bytes, st));
     char *q = (char *)buf.p;
     double *R = (double *)q; q += (size_t)nk * sizeof(double);
@@ -652,31 +595,9 @@ rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, doub
     double *outer_sc = (double *)q;       // [0,k) colsum, [k,2k) |R|^2, [2k,3k) |B|^2
     double *it_sc = outer_sc + 8 * (size_t)k;
     double *parts = it_sc + (sc_count - 8 * (size_t)k);   // [3][PMAX] fixed-order block parts
-    float *hsum = (float *)(parts + 3 * (size_t)PMAX);   // [hc_n] heavy-chunk sums
-    const size_t shk = (size_t)k * sizeof(double), shk2 = 2 * shk;
-    if (k > 1 && shk2 > 48 * 1024) {
-        // the k-column kernels keep k (inner_update 2k) per-column doubles in
-        // shared memory: above the default 48 KB they must opt in
-        int dev_ = 0, optin = 0;
-        cudaGetDevice(&dev_);
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev_);
-        if (shk2 > (size_t)optin)
-            return set_error(RWC_ERR_UNSUPPORTED, "%d right-hand sides need %zu bytes of shared memory per "
-                             "block (the device allows %d)", k, shk2, optin);
-        RWC_CUDA_TRY(cudaFuncSetAttribute(center64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shk));
-        RWC_CUDA_TRY(cudaFuncSetAttribute(colsum64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shk));
-        RWC_CUDA_TRY(cudaFuncSetAttribute(inner_start, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shk));
-        RWC_CUDA_TRY(cudaFuncSetAttribute(inner_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shk2));
-        cudaError_t ae = cudaSuccess;
-        dispatch(g, [&](auto o64, auto wt) {
-            constexpr bool O = decltype(o64)::value, Wt = decltype(wt)::value;
-            if (ae == cudaSuccess)
-                ae = cudaFuncSetAttribute(spmm32<O, Wt>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shk);
-            if (ae == cudaSuccess)
-                ae = cudaFuncSetAttribute(resid64<O, Wt>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shk);
-        });
-        RWC_CUDA_TRY(ae);
-    }
+    double *cparts = parts + 3 * (size_t)PMAX;          // k > 1: [2][k][nbc] column parts
+    float *hsum = (float *)(cparts + 2 * (size_t)k * nbc);   // [hc_n] heavy-chunk sums
+    const size_t shk = (size_t)k * sizeof(double);
     const unsigned gs = grid_for(nk), gw = grid_for(n * 32);
     const int vw = pick_vw(g);
     const unsigned gv = grid_for(n * vw);
@@ -686,6 +607,20 @@ rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, doub
         ::rwc::count_launches(1);
         sum_parts<<<1, TPB, 0, st>>>(parts, (int)blocks, PMAX, nvals, out);
     };
+    // k > 1: fixed-order per-column sums of f(A, B) into o1 (and o2)
+    double *cp2 = cparts + (size_t)k * nbc;
+    auto col_sum = [&](auto op, const auto *A, const auto *Bv, double *o1, double *o2) {
+        constexpr int OP = decltype(op)::value;
+        using T = std::remove_cv_t<std::remove_pointer_t<decltype(A)>>;
+        ::rwc::count_launches(2);
+        col_parts<OP, T><<<nbc, TPB, 0, st>>>(n, k, A, Bv, cparts, cp2);
+        sum_cols<<<(unsigned)k, TPB, 0, st>>>(cparts, (int)nbc, o1);
+        if (OP == COL_DOT2) { ::rwc::count_launches(1); sum_cols<<<(unsigned)k, TPB, 0, st>>>(cp2, (int)nbc, o2); }
+    };
+    using op_sum = std::integral_constant<int, COL_SUM>;
+    using op_sq = std::integral_constant<int, COL_SQ>;
+    using op_dot = std::integral_constant<int, COL_DOT>;
+    using op_dot2 = std::integral_constant<int, COL_DOT2>;
     int dev = 0, coop = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
@@ -706,7 +641,7 @@ rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, doub
                         <<<gv, TPB, 0, st>>>(g, B, X, R, parts);
                 });
             } else {
-                resid64<decltype(o64)::value, decltype(wt)::value><<<gw, TPB, shk, st>>>(g, k, B, X, R, outer_sc);
+                resid64<decltype(o64)::value, decltype(wt)::value><<<gw, TPB, 0, st>>>(g, k, B, X, R);
             }
         });
         if (k == 1) {
@@ -714,7 +649,9 @@ rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, doub
             ::rwc::count_launches(1); center1<<<gs, TPB, 0, st>>>(n, R, outer_sc, parts);
             finish_sum(gs, 1, outer_sc + 1);
         } else {
-            ::rwc::count_launches(1); center64<<<gs, TPB, shk, st>>>(n, k, R, outer_sc, outer_sc + k);
+            col_sum(op_sum{}, (const double *)R, (const double *)nullptr, outer_sc, nullptr);
+            ::rwc::count_launches(1); center64<<<gs, TPB, 0, st>>>(n, k, R, outer_sc);
+            col_sum(op_sq{}, (const double *)R, (const double *)nullptr, outer_sc + k, nullptr);
         }
         RWC_CUDA_TRY(cudaGetLastError());
         RWC_CUDA_TRY(cudaMemcpyAsync(h.data(), outer_sc, 2 * shk, cudaMemcpyDeviceToHost, st));
@@ -739,7 +676,8 @@ rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, doub
             ::rwc::count_launches(1); inner_start1<<<gs, TPB, 0, st>>>(n, R, outer_sc + 1, g.dinv32, r, e, z, p, parts);
             finish_sum(gs, 1, it_sc + 1);
         } else {
-            ::rwc::count_launches(1); inner_start<<<gs, TPB, shk, st>>>(n, k, R, outer_sc + k, g.dinv32, r, e, z, p, it_sc + 1 * k);
+            ::rwc::count_launches(1); inner_start<<<gs, TPB, 0, st>>>(n, k, R, outer_sc + k, g.dinv32, r, e, z, p);
+            col_sum(op_dot{}, (const float *)r, (const float *)z, it_sc + 1 * k, nullptr);
         }
         if (k == 1 && coop_ok) {
             // one cooperative launch for the whole inner solve
@@ -796,7 +734,7 @@ rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, doub
                                 <<<gv, TPB, 0, st>>>(g, p, Qv, parts);
                         });
                     } else {
-                        spmm32<decltype(o64)::value, decltype(wt)::value><<<gw, TPB, shk, st>>>(g, k, p, Qv, pq);
+                        spmm32<decltype(o64)::value, decltype(wt)::value><<<gw, TPB, 0, st>>>(g, k, p, Qv);
                     }
                 });
                 if (k == 1) {
@@ -805,7 +743,9 @@ rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, doub
                     inner_update1<<<gs, TPB, 0, st>>>(n, rz0, pq, g.dinv32, p, Qv, e, r, z, parts, PMAX);
                     finish_sum(gs, 2, rz1);   // rz1, then rr1 = rz1 + 1
                 } else {
-                    ::rwc::count_launches(1); inner_update<<<gs, TPB, shk2, st>>>(n, k, rz0, pq, g.dinv32, p, Qv, e, r, z, rz1, rr1);
+                    col_sum(op_dot{}, (const float *)p, (const float *)Qv, pq, nullptr);
+                    ::rwc::count_launches(1); inner_update<<<gs, TPB, 0, st>>>(n, k, rz0, pq, g.dinv32, p, Qv, e, r, z);
+                    col_sum(op_dot2{}, (const float *)r, (const float *)z, rz1, rr1);
                 }
                 ::rwc::count_launches(1); inner_dir<<<gs, TPB, 0, st>>>(n, k, rz0, rz1, z, p);
             }
@@ -834,8 +774,8 @@ rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, doub
         ::rwc::count_launches(1); center1<<<gs, TPB, 0, st>>>(n, X, outer_sc, parts);
         finish_sum(gs, 1, outer_sc + 1);
     } else {
-        ::rwc::count_launches(1); colsum64<<<gs, TPB, shk, st>>>(n, k, X, outer_sc);
-        ::rwc::count_launches(1); center64<<<gs, TPB, shk, st>>>(n, k, X, outer_sc, outer_sc + k);
+        col_sum(op_sum{}, (const double *)X, (const double *)nullptr, outer_sc, nullptr);
+        ::rwc::count_launches(1); center64<<<gs, TPB, 0, st>>>(n, k, X, outer_sc);
     }
     RWC_CUDA_TRY(cudaGetLastError());
     if (iters_out) *iters_out = total_iters;

@@ -138,3 +138,32 @@ def test_exact_gradient_with_more_right_hand_sides_than_default_shared_memory():
     gg = G.grad(torch.tensor(c, dtype=torch.float64, device="cuda"), k=0, tol=1e-10).double().cpu().numpy()
     a, b, w = _edges(g)
     _assert_per_edge(gg, og.grad_closed(g.n, a, b, w, c), 1e-3)
+
+
+@pytest.mark.parametrize("k,signed", [(64, False), (64, True), (0, False)])
+def test_gradient_is_bit_reproducible(k, signed):
+    """Every sum of the block CG and of the gradient assembly runs in a fixed
+    order (column parts added in block order, no floating-point atomics), so
+    the same input gives the same gradient bits on every call."""
+    g = synth.rgg(1500 if k else 300, 10.0, seed=8, sigma=0.5)
+    G = rwc.Graph.from_synth(g)
+    c = synth.uniform_vector(g.n, 5) - (0.5 if signed else 0.0)
+    ct = torch.tensor(c, dtype=torch.float64, device="cuda")
+    outs = [G.grad(ct, k=k, sketch_seed=3, tol=1e-8) for _ in range(3)]
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+
+
+def test_block_solve_is_bit_reproducible():
+    g = synth.rmat(12, 16, seed=3, sigma=1.0)
+    G = rwc.Graph.from_synth(g)
+    B = torch.randn(5, g.n, dtype=torch.float64, device="cuda",
+                    generator=torch.Generator(device="cuda").manual_seed(1))
+    B -= B.mean(dim=1, keepdim=True)
+    outs = []
+    for _ in range(3):
+        X = torch.empty_like(B)
+        rwc.rwc_solve(G.handle, 5, B, X, 1e-9)
+        outs.append(X)
+    for X in outs[1:]:
+        assert torch.equal(X, outs[0])

@@ -127,3 +127,14 @@ def test_fastwalk_auto_uses_the_algorithms_parameters():
     assert np.all(pi * np.abs(H.cpu().numpy() - Hx) <= eps)
     with pytest.raises(ValueError):
         rwc.fastwalk_auto(rwc.Graph.from_synth(synth.ba(2000, 3, seed=0)), 0.3)   # l ~ 3e8
+
+
+def test_auto_params_are_bit_reproducible():
+    # the inverse iteration's sums and its Laplacian solves run in a fixed
+    # order, so lambda (and with it t, l and theta) has the same bits every call
+    g = synth.rmat(13, 16, seed=2, sigma=1.0)
+    G = rwc.Graph.from_synth(g)
+    ps = [rwc.rwc_auto_params(G.handle, 0.1) for _ in range(3)]
+    for p in ps[1:]:
+        for f, _ in p._fields_:
+            assert getattr(p, f) == getattr(ps[0], f), f
