@@ -129,9 +129,9 @@ def test_exact_gradient_on_parallel_arcs():
     assert same.any() and np.allclose(gg[1:][same], gg[:-1][same], rtol=1e-6, atol=0)
 
 
-def test_exact_gradient_with_more_right_hand_sides_than_default_shared_memory():
-    # n + 2 = 3302 right-hand sides: the solve's per-column shared memory
-    # (2 x 3302 doubles) is above the default 48 KB and must be opted into
+def test_exact_gradient_with_thousands_of_right_hand_sides():
+    # n + 2 = 3302 right-hand sides, more than a block's threads: the column
+    # sums take the path where each thread owns several columns
     g = synth.rgg(3300, 10.0, seed=5, sigma=0.5)
     G = rwc.Graph.from_synth(g)
     c = synth.uniform_vector(g.n, 21)
