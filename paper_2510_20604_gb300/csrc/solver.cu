@@ -417,7 +417,32 @@ __global__ void __launch_bounds__(TPB) cg1_coop(DevGraph g, const float *__restr
     for (; it < max_it; ++it) {
         // q = L p and <p, q>
         double acc = 0.0;
-        if (g.bin_rows) {
+        bool done = false;
+        if constexpr (!W && !OFF64) {
+            if (g.ell) {
+                // bounded degree: one thread per row over its inline neighbour
+                // list (one or two 16-byte loads), the heads' p gathered in
+                // arc order
+                const int ew4 = g.ell_w / 4;
+                for (int64_t u = tid; u < g.n; u += nthr) {
+                    float s = 0.f;
+                    for (int i = 0; i < ew4; ++i) {
+                        const int4 c4 = __ldg(g.ell + u * ew4 + i);
+                        if (c4.x >= 0) s += p[c4.x];
+                        if (c4.y >= 0) s += p[c4.y];
+                        if (c4.z >= 0) s += p[c4.z];
+                        if (c4.w >= 0) s += p[c4.w];
+                    }
+                    const float pu = p[u];
+                    const float qu = (float)g.d[u] * pu - s;
+                    q[u] = qu;
+                    acc += (double)pu * (double)qu;
+                }
+                done = true;
+            }
+        }
+        if (done) {
+        } else if (g.bin_rows) {
             // rows by degree bin, each bin with as many lanes per row as its degrees
             acc += spmv_bin<2, OFF64, W>(g, g.bin_rows + g.bin_off[0], g.bin_off[1] - g.bin_off[0], p, q, tid, nthr);
             acc += spmv_bin<4, OFF64, W>(g, g.bin_rows + g.bin_off[1], g.bin_off[2] - g.bin_off[1], p, q, tid, nthr);
