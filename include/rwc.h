@@ -51,7 +51,7 @@ enum {
     RWC_ERR_OOM = 3,            /* device or host allocation failed */
     RWC_ERR_NOT_CONVERGED = 4,  /* an iteration cap was reached */
     RWC_ERR_CUDA = 5,           /* a CUDA call failed */
-    RWC_ERR_UNSUPPORTED = 6     /* valid request this build cannot serve */
+    RWC_ERR_UNSUPPORTED = 6     /* valid request the library cannot serve */
 };
 
 typedef struct CUstream_st *rwc_stream_t;   /* same type as cudaStream_t */
