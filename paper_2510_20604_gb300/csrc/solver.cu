@@ -717,6 +717,12 @@ rwc_status solve_nodemajor(rwc_graph *G, int k, const double *B, double *X, doub
                     int per_sm = 0;
                     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TPB, 0);
                     if (per_sm < 1) return;
+                    // at most 4 blocks per SM (6 fit): fewer blocks make each grid
+                    // synchronisation and fixed-order sum cheaper, which the
+                    // latency-bound iterations of large-diameter graphs feel most
+                    // (1024² grid 0.48 -> 0.37 s; R-MAT 24 the same; 3 per SM slows
+                    // the bandwidth-heavier R-MAT solves)
+                    per_sm = std::min(per_sm, 4);
                     const unsigned blocks = (unsigned)std::min<int64_t>(std::min<int64_t>((int64_t)num_sms() * per_sm, gv), PMAX);
                     const float *dinv = g.dinv32;
                     float *rr_ = r, *ee = e, *zz = z, *pp = p, *qq = Qv, *hs = hsum;
