@@ -98,3 +98,17 @@ def test_evaluation_and_walk_entry_points_reject_bad_arguments():
     # rwc_trap_walks / rwc_auto_params: a graph is required
     assert L.rwc_trap_walks(None, 1, 4, 100, 8, None, None) == 1
     assert L.rwc_auto_params(None, 0.1, 0, 0.0, None, None) == 1
+
+
+def test_status_pivot_and_sampling_entry_points_reject_bad_arguments():
+    """rwc_sync_status, rwc_pivot_solve, rwc_sample_trees and the allocation-
+    free sampler check their handles and ranges on the host, before any
+    device work."""
+    L = rwc.lib()
+    assert L.rwc_sync_status(None, None) == 1
+    assert "NULL" in rwc.rwc_last_error()
+    assert L.rwc_pivot_solve(None, 1e-10, 8, None) == 1
+    assert L.rwc_sample_trees(None, 1, 0, 4, 8, None, None, None, None, None) == 1
+    assert L.rwc_sample_trees_noalloc(None, 1, 0, 4, 8, None, None, None) == 1
+    assert L.rwc_estimate(None, 8, 4, 1e-10, 8, None, None) == 1
+    assert L.rwc_recover(None, 8, 4, 8, 8, None) == 1
