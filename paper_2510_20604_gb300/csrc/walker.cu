@@ -120,18 +120,18 @@ __device__ __forceinline__ uint64_t gtimer() {
 // that may be drawn), then the stores, the claim CAS and the successor draw,
 // whose arc load overlaps the CAS (on graphs of degree at most 8 the draw
 // picks from an inline row loaded beside the word, with no arc load).  The
-// lanes of a warp thus pay about two dependent memory round trips per tick,
+// lanes of a warp thus pay about two dependent memory round trips per step,
 // whatever mix of states they are in.  Waits poll shared memory or the one
 // vertex word.  (Loading the next tick's word at the end of a tick, while a
 // claim is in flight, was measured slower on every graph: 29% on a 256² grid,
 // 43% on a 1024² grid, 24% on R-MAT 20.)
 enum : int { S_IDLE = 0, S_WALK, S_POP, S_REL, S_SET, S_WAITK, S_WAITV, S_WAITH, S_DONE };
 
-// Register cap of the walker kernel: at most 56 registers are used without
-// spills (52 without inline rows of 8), which keeps 18 blocks of 64 walkers
-// per SM resident, 2736 trees on 152 SMs.  (A cap of 40 lets 96-walker blocks
-// keep 2000 trees resident, but its spills cost more than the extra walkers
-// gain.)
+// Register cap of the walker kernel: 52 registers are used without spills
+// (56 with inline rows of 4, 58 with rows of 8), which keeps 16 to 18 blocks
+// of 64 walkers per SM resident, at least 2432 trees on 152 SMs.  (A cap of
+// 40 lets 96-walker blocks keep 2000 trees resident, but its spills cost more
+// than the extra walkers gain.)
 #ifndef RWC_WALKER_MAXNREG
 #define RWC_WALKER_MAXNREG 64
 #endif
