@@ -19,9 +19,9 @@
  *    owns and frees in the matching *_destroy call.
  *  - stream is a cudaStream_t (NULL = the legacy default stream).  Work is
  *    enqueued on it; entry points that must inspect device results
- *    (rwc_sample_trees, rwc_sample_trees_noalloc, rwc_estimate, rwc_solve,
- *    rwc_grad, rwc_batch_sample, rwc_trap_walks, rwc_auto_params,
- *    rwc_predict_mre) synchronise
+ *    (rwc_sample_trees, rwc_sample_trees_noalloc, rwc_estimate,
+ *    rwc_pivot_solve, rwc_recover, rwc_solve, rwc_grad, rwc_batch_sample,
+ *    rwc_trap_walks, rwc_auto_params, rwc_predict_mre) synchronise
  *    that stream before returning, so their outputs are ready on return and
  *    device-side errors come back as their status.  rwc_sample_trees with
  *    rwc_options_t.async_status = 1 is the exception: it only enqueues, its
