@@ -112,3 +112,34 @@ def test_status_pivot_and_sampling_entry_points_reject_bad_arguments():
     assert L.rwc_sample_trees_noalloc(None, 1, 0, 4, 8, None, None, None) == 1
     assert L.rwc_estimate(None, 8, 4, 1e-10, 8, None, None) == 1
     assert L.rwc_recover(None, 8, 4, 8, 8, None) == 1
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """The ctypes mirrors of rwc_graph_info_t, rwc_options_t, rwc_stats_t and
+    rwc_params_t have the C structs' sizes and field offsets (a C program
+    compiled against include/rwc.h prints them)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_2510_20604_gb300 import _binding as B
+    pairs = [("rwc_graph_info_t", B.GraphInfo), ("rwc_options_t", B.Options),
+             ("rwc_stats_t", B.Stats), ("rwc_params_t", B.Params)]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "rwc.h"', "int main(void) {"]
+    for cname, py in pairs:
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            cf = "lambda" if f == "lambda_" else f
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {cf}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in pairs:
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
